@@ -1,0 +1,235 @@
+"""PDHG with PDLP's adaptive steps, restarts and termination (oracle; test infrastructure).
+
+Iteration (Sec. II.E, read in the general form of ``oracle.lp``), in the
+rescaled space of ``oracle.scaling``, with step eta and primal weight omega,
+tau = eta / omega and sigma = eta * omega:
+
+  x+ = proj_[l, u]( x - tau (c - K^T y) )                      (primal step)
+  y+ = proj_[y_lo, inf)( y + sigma (q - K (2 x+ - x)) )        (dual step)
+
+The paper cites Applegate et al. for adaptive step sizes and restarts without
+stating them (Sec. II.E).  Readings used here (the GPU solver follows the same
+ones; its code shares nothing with this file):
+
+* step rule: with dx = x+ - x, dy = y+ - y and k the 1-based count of step
+  attempts so far,
+      eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy^T K dx|)   (inf if 0)
+      eta'    = min((1 - (k+1)^-0.3) eta_max, (1 + (k+1)^-0.6) eta)
+  the attempt is accepted iff eta <= eta_max; either way eta <- eta'.
+  eta_0 = 1 / max|K~_ij|;  omega_0 = ||c~|| / ||q~|| (1 if either < 1e-10).
+* averages: step-size weighted averages of accepted iterates since the last
+  restart.
+* every ``check_every`` attempts: rel-KKT (``oracle.lp``) of the current and the
+  average iterate on the unscaled LP; stop when either is <= tol (the smaller
+  wins).  Restart candidate = the one with smaller
+      KKT_omega = sqrt(omega ||r~_p||^2 + ||r~_d||^2 / omega + (P - D)^2)
+  (scaled residuals).  Restart iff KKT_omega(cand) <= 0.2 KKT_0, or
+  (<= 0.8 KKT_0 and > the previous check's value), or the attempts since the
+  last restart are >= 0.36 of all attempts.  On restart, with
+  Dx = ||x_cand - x_anchor||, Dy = ||y_cand - y_anchor||, if both > 1e-10:
+      omega <- exp(0.5 log(Dy / Dx) + 0.5 log omega)
+  the iterate, anchor and KKT_0 move to the candidate (KKT_0 taken with the
+  new omega, which also becomes the "previous" value) and the averages reset.
+
+``schedule`` replays a recorded run: per attempt (eta, omega, accepted) and per
+check (restart, to_average); the oracle then follows those decisions while still
+computing and returning its own, so that both can be compared.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .lp import LP, kkt, project_reduced_cost
+from .scaling import rescale
+
+
+@dataclass
+class PDLPOptions:
+    check_every: int = 64
+    beta_sufficient: float = 0.2
+    beta_necessary: float = 0.8
+    beta_artificial: float = 0.36
+    omega_smoothing: float = 0.5
+    step_reduction_exp: float = 0.3
+    step_growth_exp: float = 0.6
+    ruiz_iters: int = 10
+    pock_chambolle: bool = True
+
+
+@dataclass
+class PDHGResult:
+    x: np.ndarray            # unscaled primal
+    y: np.ndarray            # unscaled dual
+    x_scaled: np.ndarray
+    y_scaled: np.ndarray
+    status: str
+    attempts: int
+    accepted: int
+    restarts: int
+    rel_kkt: float
+    primal_obj: float
+    dual_obj: float
+    eta: float
+    omega: float
+    Dr: np.ndarray
+    Dc: np.ndarray
+    attempt_log: list = field(default_factory=list)  # (eta, omega, accepted, eta_max)
+    check_log: list = field(default_factory=list)    # dict per check
+
+
+def _kkt_omega(slp: LP, Dr, Dc, lp: LP, x_s, y_s, omega):
+    """Scaled-space restart metric and unscaled rel-KKT of one candidate."""
+    res = kkt(lp, Dc * x_s, Dr * y_s)
+    rp_s = Dr * res.rp
+    rd_s = Dc * res.rd
+    gap = res.primal_obj - res.dual_obj
+    val = np.sqrt(omega * (rp_s @ rp_s) + (rd_s @ rd_s) / omega + gap * gap)
+    return float(val), res
+
+
+def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: PDLPOptions | None = None,
+               schedule: dict | None = None, fixed: dict | None = None, record: bool = False,
+               stop_after: int | None = None, start: tuple | None = None) -> PDHGResult:
+    """Solve ``lp`` to rel-KKT <= tol.
+
+    fixed      -- dict(eta=..., omega=...): constant steps, every attempt accepted, no
+                  restarts; runs exactly ``stop_after`` attempts.
+    schedule   -- dict(attempts=[(eta, omega, accepted), ...], checks=[(restart, to_avg), ...])
+    stop_after -- stop after this many attempts (status "stopped").
+    start      -- (x, y) of the ORIGINAL LP to start from instead of the projection of 0.
+    """
+    opts = opts or PDLPOptions()
+    slp, Dr, Dc = rescale(lp, opts.ruiz_iters, opts.pock_chambolle)
+    K, KT = slp.K, slp.K.T.tocsr()
+    c, q, l, u = slp.c, slp.q, slp.l, slp.u
+    y_lo = slp.dual_lower()
+
+    if start is None:
+        x = np.clip(np.zeros(slp.n), l, u)
+        y = np.maximum(np.zeros(slp.m), y_lo)
+    else:
+        x = np.clip(np.asarray(start[0], np.float64) / Dc, l, u)
+        y = np.maximum(np.asarray(start[1], np.float64) / Dr, y_lo)
+    Kx = K @ x
+    KTy = KT @ y
+    absmax = np.abs(K.data).max() if K.nnz else 1.0
+    eta = 1.0 / absmax
+    cn, qn = np.linalg.norm(c), np.linalg.norm(q)
+    omega = cn / qn if (cn > 1e-10 and qn > 1e-10) else 1.0
+    if fixed is not None:
+        eta, omega = float(fixed["eta"]), float(fixed["omega"])
+
+    k = 0
+    accepted = 0
+    restarts = 0
+    since_restart = 0
+    xa, ya = x.copy(), y.copy()
+    xsum = np.zeros(slp.n)
+    ysum = np.zeros(slp.m)
+    wsum = 0.0
+    kkt0, _ = _kkt_omega(slp, Dr, Dc, lp, x, y, omega)
+    kkt_prev = kkt0
+    attempt_log, check_log = [], []
+    sched_a = schedule["attempts"] if schedule else None
+    sched_c = schedule["checks"] if schedule else None
+    n_check = 0
+    status = "iteration_limit"
+    final = None
+
+    while True:
+        for _ in range(opts.check_every):
+            if k >= max_attempts or (stop_after is not None and k >= stop_after):
+                break
+            if sched_a is not None:
+                eta, omega = float(sched_a[k][0]), float(sched_a[k][1])
+            tau, sigma = eta / omega, eta * omega
+            xn = np.clip(x - tau * (c - KTy), l, u)
+            Kxn = K @ xn
+            yn = np.maximum(y + sigma * (q - 2.0 * Kxn + Kx), y_lo)
+            dx, dy = xn - x, yn - y
+            movement = omega * (dx @ dx) + (dy @ dy) / omega
+            interaction = 2.0 * abs(dy @ (Kxn - Kx))
+            eta_max = movement / interaction if interaction > 0 else np.inf
+            k += 1
+            eta_next = min((1.0 - (k + 1) ** (-opts.step_reduction_exp)) * eta_max,
+                           (1.0 + (k + 1) ** (-opts.step_growth_exp)) * eta)
+            ok = ok_own = eta <= eta_max
+            if fixed is not None:
+                ok, eta_next = True, eta
+            if sched_a is not None:
+                ok = bool(sched_a[k - 1][2])
+            if record:
+                attempt_log.append((eta, omega, int(ok), eta_max, eta_next, int(ok_own)))
+            if ok:
+                xsum += eta * xn
+                ysum += eta * yn
+                wsum += eta
+                x, y, Kx = xn, yn, Kxn
+                KTy = KT @ y
+                accepted += 1
+            since_restart += 1
+            eta = eta_next
+        stop_now = k >= max_attempts or (stop_after is not None and k >= stop_after)
+        if fixed is not None or (stop_now and k % opts.check_every != 0):
+            if stop_now:
+                status = "stopped"
+                break
+            continue
+        if wsum > 0:
+            xbar, ybar = xsum / wsum, ysum / wsum
+        else:
+            xbar, ybar = x, y
+        kc_cur, res_cur = _kkt_omega(slp, Dr, Dc, lp, x, y, omega)
+        kc_avg, res_avg = _kkt_omega(slp, Dr, Dc, lp, xbar, ybar, omega)
+        entry = dict(attempts=k, kkt_cur=kc_cur, kkt_avg=kc_avg, rel_cur=res_cur.rel_kkt,
+                     rel_avg=res_avg.rel_kkt, omega=omega)
+        best_avg = res_avg.rel_kkt < res_cur.rel_kkt
+        if min(res_cur.rel_kkt, res_avg.rel_kkt) <= tol:
+            final = (xbar, ybar, res_avg) if best_avg else (x, y, res_cur)
+            status = "optimal"
+            entry.update(restart=False, to_avg=False)
+            check_log.append(entry)
+            break
+        to_avg = kc_avg < kc_cur
+        kc = kc_avg if to_avg else kc_cur
+        restart = (kc <= opts.beta_sufficient * kkt0) or \
+                  (kc <= opts.beta_necessary * kkt0 and kc > kkt_prev) or \
+                  (since_restart >= opts.beta_artificial * k)
+        entry.update(restart_own=restart, to_avg_own=to_avg)
+        if sched_c is not None:
+            restart, to_avg = bool(sched_c[n_check][0]), bool(sched_c[n_check][1])
+            kc = kc_avg if to_avg else kc_cur
+        entry.update(restart=restart, to_avg=to_avg)
+        kkt_prev = kc
+        if restart:
+            xc, yc = (xbar, ybar) if to_avg else (x, y)
+            dxr, dyr = np.linalg.norm(xc - xa), np.linalg.norm(yc - ya)
+            if dxr > 1e-10 and dyr > 1e-10:
+                w = opts.omega_smoothing
+                omega = float(np.exp(w * np.log(dyr / dxr) + (1 - w) * np.log(omega)))
+            x, y = xc.copy(), yc.copy()
+            Kx, KTy = K @ x, KT @ y
+            xa, ya = x.copy(), y.copy()
+            xsum[:] = 0.0
+            ysum[:] = 0.0
+            wsum = 0.0
+            since_restart = 0
+            restarts += 1
+            kkt0, _ = _kkt_omega(slp, Dr, Dc, lp, x, y, omega)
+            kkt_prev = kkt0
+        entry["omega_after"] = omega
+        check_log.append(entry)
+        n_check += 1
+        if stop_now:
+            status = "iteration_limit" if k >= max_attempts else "stopped"
+            break
+
+    if final is None:
+        final = (x, y, kkt(lp, Dc * x, Dr * y))
+    xs, ys, res = final
+    return PDHGResult(x=Dc * xs, y=Dr * ys, x_scaled=xs, y_scaled=ys, status=status, attempts=k,
+                      accepted=accepted, restarts=restarts, rel_kkt=res.rel_kkt, primal_obj=res.primal_obj,
+                      dual_obj=res.dual_obj, eta=eta, omega=omega, Dr=Dr, Dc=Dc,
+                      attempt_log=attempt_log, check_log=check_log)

@@ -1,0 +1,83 @@
+"""Instance generator invariants (host only)."""
+import numpy as np
+import pytest
+
+from paper_2512_06715_gb300.instances import (ROW_BALANCE, ROW_FLOW_NEG, ROW_FLOW_POS, ROW_LOGIC,
+                                              VAR_THETA, build_instance, workload)
+from tests.conftest import instance_lp
+
+
+def test_counts_tiny():
+    inst = workload("uc24_g33_T24")
+    G, N, L, T = 33, 24, 38, 24
+    assert inst.n == T * (4 * G + N)
+    m_expect = N * T + G * (T - 1) + 2 * L * T + 2 * G * T + 2 * G * (T - 1) + 2 * G * (T - 1)
+    assert inst.m == m_expect
+    assert inst.m_eq == N * T + G * (T - 1)
+    assert np.all(inst.row_kind[: inst.m_eq] <= ROW_LOGIC)
+    assert np.all(inst.row_kind[inst.m_eq:] >= ROW_FLOW_POS)
+    assert np.all(np.diff(inst.row_ptr) >= 1)
+
+
+def test_csr_sorted_unique():
+    inst = workload("uc24_g33_T24")
+    for i in range(inst.m):
+        cols = inst.col[inst.row_ptr[i]:inst.row_ptr[i + 1]]
+        assert np.all(np.diff(cols) > 0)
+
+
+def test_network_rows():
+    inst = workload("uc24_g33_T24")
+    A = inst.scipy_csr().tocsr()
+    theta = inst.var_kind == VAR_THETA
+    bal = np.where(inst.row_kind == ROW_BALANCE)[0]
+    # Laplacian part of every balance row sums to zero (flows conserve power)
+    s = np.asarray(A[bal][:, theta].sum(axis=1)).ravel()
+    assert np.allclose(s, 0.0, atol=1e-9 * np.abs(A.data).max())
+    # the two flow-limit rows of each line are negatives of each other
+    fp = np.where(inst.row_kind == ROW_FLOW_POS)[0]
+    fn = np.where(inst.row_kind == ROW_FLOW_NEG)[0]
+    assert len(fp) == len(fn)
+    assert abs(A[fp] + A[fn]).max() == 0.0
+
+
+def test_all_on_dispatch_feasible():
+    """The proportional all-on dispatch that the line-limit floor is built for is
+    feasible, so the relaxation is feasible by construction."""
+    from oracle.lp import max_violation
+    inst = workload("uc24_g33_T24")
+    lp = instance_lp(inst)
+    T, G = inst.idx_p.shape
+    x = np.zeros(inst.n)
+    D = inst.load.sum(axis=1)
+    share = inst.gen_pmax / inst.gen_pmax.sum()
+    for t in range(T):
+        x[inst.idx_p[t]] = D[t] * share
+        x[inst.idx_u[t]] = 1.0
+    # angles: solve the balance rows for theta (grounded at bus 0)
+    A = inst.scipy_csr().tocsr()
+    bal = inst.row_balance
+    import scipy.sparse.linalg as spla
+    for t in range(T):
+        rows = bal[t]
+        th = inst.idx_theta[t]
+        rhs = inst.q[rows] - A[rows] @ x
+        B = A[rows][:, th[1:]]
+        sol = spla.lsqr(B, rhs, atol=1e-14, btol=1e-14, iter_lim=10000)[0]
+        x[th[1:]] = sol
+    assert max_violation(lp, x) <= 1e-6 * np.abs(inst.q).max()
+
+
+def test_invalid_params():
+    with pytest.raises(ValueError):
+        build_instance(0, 0, 1, 1)
+    with pytest.raises(ValueError):
+        build_instance(5, 3, 1, 1)  # fewer lines than the ring needs
+
+
+def test_deterministic():
+    a = workload("uc24_g33_T24", seed=3)
+    b = workload("uc24_g33_T24", seed=3)
+    c = workload("uc24_g33_T24", seed=4)
+    assert np.array_equal(a.val, b.val) and np.array_equal(a.q, b.q)
+    assert not np.array_equal(a.q, c.q)
