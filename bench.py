@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 PDHG hot path on a synthetic DC unit-commitment relaxation.
+
+One JSON line on stdout (rank 0).  Headline: effective SpMV HBM GB/s of the
+mixed-precision (FP32 iterates, FP64 KKT/refinement) PDHG on the 6717-bus,
+96-period relaxation -- the algorithmic bytes of the two fused SpMV kernels
+(K x' + dual step, K^T y' + primal step) of every step attempt, divided by the
+device time of whole solver calls.  A step is one pdhg_solve call from a cold
+start capped at --attempts step attempts: Ruiz + Pock-Chambolle rescaling, the
+FP32 copies, PDHG attempts, an FP64 KKT check with restart/primal-weight logic
+every 64 attempts and the output.  The same step in plain FP64, the
+time-to-tolerance of both precisions (capped), the dominant kernel's roofline,
+an end-to-end run through host buffers and the CPU oracle are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank solves its own replica (the LP does not shard:
+replicas only) and rank 0 reports the whole-job aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "SpMV HBM GB/s (mixed-precision PDHG; time to rel-KKT 1e-8 and node LPs/s reported beside)"
+DEFAULT_WORKLOAD = "uc6717_g1000_T96"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--attempts", type=int, default=4096, help="step attempts per solver call")
+    p.add_argument("--ttt-limit", type=float, default=40.0,
+                   help="seconds cap of each time-to-tolerance solve (0 = skip)")
+    p.add_argument("--cpu-attempts", type=int, default=64, help="oracle attempts of the CPU sample")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--host-loop", action="store_true",
+                   help="launch the per-check bodies from the host instead of one CUDA graph "
+                        "(same kernels; profilers cannot see kernels inside conditional graphs)")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+def algorithmic_bytes(n, m, nnz, elt):
+    """Per attempt, CSR-equivalent: matrix stream (value + int32 column + int32 row
+    pointer) of K and K^T, each gathered vector once, each streamed vector once."""
+    dual = nnz * (elt + 4) + 4 * m + elt * n + elt * m * (8 if elt == 4 else 7)
+    adj = nnz * (elt + 4) + 4 * n + elt * m + elt * n * 8
+    return dual, adj
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks() -> dict:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def dram_traffic_record(kernel_src: Path):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    rec = ROOT / "profiles" / "dram_traffic.json"
+    if not rec.exists():
+        return None
+    d = json.loads(rec.read_text())
+    h = hashlib.sha256(kernel_src.read_bytes()).hexdigest()[:16]
+    if d.get("kernel_source_sha256_16") != h:
+        return None
+    return d
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def cpu_oracle_gbs(inst, attempts: int):
+    """The FP64 CPU oracle timed on the host cores on a bounded sample: one
+    oracle solve (rescaling included) capped at `attempts` step attempts."""
+    from oracle.lp import lp_from_arrays
+    from oracle.pdhg import pdhg_solve
+    lp = lp_from_arrays(inst.row_ptr, inst.col, inst.val, inst.q, inst.c, inst.l, inst.u, inst.m_eq)
+    t0 = time.perf_counter()
+    pdhg_solve(lp, tol=1e-30, stop_after=attempts)
+    dt = time.perf_counter() - t0
+    d, a = algorithmic_bytes(inst.n, inst.m, inst.nnz, 8)
+    gbs = attempts * (d + a) / dt / 1e9
+    return gbs, dt
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2512_06715_gb300.instances import workload
+    inst = workload(args.workload)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        gbs, dt = cpu_oracle_gbs(inst, args.cpu_attempts)
+        if i >= args.warmup:
+            steps.append((gbs, dt))
+    value = float(np.mean([g for g, _ in steps]))
+    ms = float(np.mean([d for _, d in steps]) * 1e3)
+    sample = f"{args.cpu_attempts} oracle attempts (rescaling included) per step on {args.workload}"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": inst.n, "m": inst.m, "nnz": inst.nnz},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2512_06715_gb300 import pdhg
+    from paper_2512_06715_gb300.instances import workload
+
+    inst = workload(args.workload)
+    n, m, nnz = inst.n, inst.m, inst.nnz
+    stream = torch.cuda.current_stream()
+
+    def opts(prec, attempts, tol=1e-8, tl=600.0):
+        return pdhg.default_opts(precision=prec, max_iters=attempts, tol=tol, time_limit_s=tl,
+                                 host_loop=int(args.host_loop))
+
+    ws = pdhg.Workspace.from_instance(inst, opts("mixed", args.attempts), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(prec, k, w):
+        ws.set_opts(precision=pdhg.PREC_MIXED if prec == "mixed" else pdhg.PREC_FP64,
+                    max_iters=args.attempts, tol=1e-8, time_limit_s=600.0)
+        res = None
+        for _ in range(w):
+            _, _, res = ws.solve()
+        barrier()
+        total = 0.0
+        launches = 0
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, res = ws.solve()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1) * 1e-3
+            launches += res["kernel_launches"]
+        barrier()
+        return total, res, launches
+
+    # headline: mixed precision
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    t_mixed, r_mixed, launches = timed("mixed", args.steps, args.warmup)
+    clk = clocks.stop()
+    t64, r64, _ = timed("fp64", max(1, args.steps // 2), 1)
+    d32, a32 = algorithmic_bytes(n, m, nnz, 4)
+    d64, a64 = algorithmic_bytes(n, m, nnz, 8)
+    att32 = r_mixed["iterations"]
+    att64 = r64["iterations"]
+    sec_per_step = t_mixed / args.steps
+    if world > 1:
+        t = torch.tensor([sec_per_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec_per_step = float(t.item())
+    value = world * att32 * (d32 + a32) / sec_per_step / 1e9
+    fp64_gbs = att64 * (d64 + a64) / (t64 / max(1, args.steps // 2)) / 1e9
+
+    # dominant kernel, timed alone on this stream with CUDA events
+    tk = ws.time_kernels(pdhg.PREC_MIXED, reps=20)
+    achieved = tk["bytes_dual"] / (tk["ms_dual"] * 1e-3) / 1e9
+    peaks = measured_peaks()
+    traffic = dram_traffic_record(ROOT / "paper_2512_06715_gb300" / "csrc" / "pdhg_kernels.cu")
+    roofline = {"bound": "hbm", "kernel": "k_dual<float> (K x' + projected dual step)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (burst)",
+                "traffic": (traffic["bytes_per_launch"] if traffic else None),
+                "algorithmic_bytes_per_launch": tk["bytes_dual"], "ms_per_launch": tk["ms_dual"],
+                "adjoint_kernel_gbs": tk["bytes_adj"] / (tk["ms_adj"] * 1e-3) / 1e9}
+
+    # end to end through host buffers: H2D of the LP values, solve, D2H of x, y
+    host = {k: ws.t[k].cpu().pin_memory() for k in ("val", "c", "l", "u", "q")}
+    xo = torch.empty(n, dtype=torch.float64).pin_memory()
+    yo = torch.empty(m, dtype=torch.float64).pin_memory()
+    ws.set_opts(precision=pdhg.PREC_MIXED, max_iters=args.attempts)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = (n + m) * 8
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_att = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        for k, v in host.items():
+            ws.t[k].copy_(v, non_blocking=True)
+        x, y, r = ws.solve()
+        xo.copy_(x, non_blocking=True)
+        yo.copy_(y, non_blocking=True)
+        e_att += r["iterations"]
+    e1.record(stream)
+    e1.synchronize()
+    e2e_s = e0.elapsed_time(e1) * 1e-3
+    e2e = {"value": world * e_att * (d32 + a32) / e2e_s / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # time to tolerance (capped), both precisions
+    ttt = {}
+    if args.ttt_limit > 0:
+        for prec in ("mixed", "fp64"):
+            ws.set_opts(precision=pdhg.PREC_MIXED if prec == "mixed" else pdhg.PREC_FP64,
+                        max_iters=10**9, tol=1e-8, time_limit_s=args.ttt_limit)
+            _, _, r = ws.solve()
+            ttt[prec] = {"status": r["status_name"], "rel_kkt": r["rel_kkt"],
+                         "seconds_to_1e-4_1e-6_1e-8": r["time_to_tol"],
+                         "attempts_to_1e-4_1e-6_1e-8": r["iters_to_tol"],
+                         "cap_s": args.ttt_limit, "attempts": r["iterations"],
+                         "attempts_per_s": r["iterations"] / r["solve_seconds"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        gbs, dt = cpu_oracle_gbs(inst, args.cpu_attempts)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_attempts} oracle attempts (rescaling included) on {args.workload}, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "m": m, "nnz": nnz,
+                       "attempts_per_step": args.attempts, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MiB buffer written between timed steps; working set > L2"},
+            "dtype_detail": "FP32 matrix and iterates, FP64 KKT/gap/restart reductions and refinement",
+            "attempts_per_s": {"mixed": att32 / sec_per_step, "fp64": att64 / (t64 / max(1, args.steps // 2))},
+            "fp64_gbs": fp64_gbs,
+            "time_to_tolerance": ttt,
+            "roofline": roofline,
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ws.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * pdhg.h -- C ABI of the GB300 PDHG solver for LP relaxations of DC unit
+ * commitment (sm_103a CUDA kernels; no host fallback).
+ *
+ * Method.  The paper solves the relaxed UC LP with the Primal-Dual Hybrid
+ * Gradient method (Sec. II.E):  x+ = proj(x + tau A^T y - tau c),
+ * y+ = y - sigma A (2x+ - x) + sigma b, with the adaptive step sizes and
+ * restarts of Applegate et al. that it cites there.  Its LP statement
+ * (min c^T x, Ax <= b, x >= 0, Sec. II.E) is sign-inconsistent with its saddle
+ * function and lacks the dual projection; this library uses the PDLP general
+ * form the cited method is defined on:
+ *
+ *     min c^T x  s.t.  K_i x = q_i (i < m_eq),  K_i x >= q_i (i >= m_eq),
+ *                      l <= x <= u                 (entries may be +-INFINITY)
+ *     L(x, y) = c^T x - y^T (K x - q),  y_i free (i < m_eq),  y_i >= 0 (i >= m_eq)
+ *
+ * Optimality is measured on the unscaled LP in FP64 (Sec. III.B names the log
+ * quantities: primal and dual objective, primal and dual residual, gap):
+ *     rel_p   = ||r_p||_2 / (1 + ||q||_2),   r_p = q - Kx (eq), (q - Kx)^+ (>=)
+ *     rel_d   = ||r_d||_2 / (1 + ||c||_2),   r_d = lambda - proj(lambda),
+ *               lambda = c - K^T y, proj keeps the sign each finite bound allows
+ *     rel_gap = |P - D| / (1 + |P| + |D|),   P = c^T x,
+ *               D = q^T y + sum_j (l_j lambda_j^+ - u_j lambda_j^-)
+ *     rel_kkt = max(rel_p, rel_d, rel_gap)
+ *
+ * Conventions for every entry point.
+ *   - Pointers documented "device" must be device memory of the current CUDA
+ *     device; "host" pointers are host memory.  The caller owns every input and
+ *     output buffer; the workspace owns its internal buffers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work of a call is enqueued on it.  Calls that return results
+ *     in host structs synchronise that stream before returning.
+ *   - Return value: PDHG_OK (0) or a negative PDHG_ERR_* code; the message of
+ *     the last failure on the calling thread is in pdhg_last_error().
+ *   - A workspace is not thread safe; use one per host thread.
+ */
+#ifndef PDHG_H
+#define PDHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes (return values) */
+#define PDHG_OK 0
+#define PDHG_ERR_INVALID_ARG (-1) /* bad pointer, size, or option             */
+#define PDHG_ERR_CUDA (-2)        /* a CUDA runtime call failed                */
+#define PDHG_ERR_NUMERIC (-3)     /* NaN/Inf in the data or the iterates       */
+#define PDHG_ERR_TIMEOUT (-4)     /* a bounded device wait gave up             */
+#define PDHG_ERR_UNSUPPORTED (-5) /* size or mode not supported (e.g. > 2^31)  */
+#define PDHG_ERR_NOMEM (-6)       /* device or host allocation failed          */
+
+/* solver outcome (pdhg_result.status) */
+#define PDHG_STATUS_OPTIMAL 1    /* rel_kkt <= tol                              */
+#define PDHG_STATUS_ITER_LIMIT 2 /* max_iters attempts done                     */
+#define PDHG_STATUS_TIME_LIMIT 3 /* time_limit_s reached (device clock)         */
+#define PDHG_STATUS_CANCELLED 4  /* *cancel_flag became nonzero                 */
+#define PDHG_STATUS_NUMERIC 5    /* NaN/Inf met in a KKT evaluation             */
+
+/* arithmetic of the iterations (KKT, restart and gap reductions are FP64 always) */
+#define PDHG_PREC_FP64 0  /* FP64 matrix, iterates and accumulation            */
+#define PDHG_PREC_MIXED 1 /* FP32 matrix/iterates + FP64 iterative refinement   */
+
+/* The LP, as device pointers in the caller's memory (read, never written).
+ * CSR of K with ascending column indices in each row, no duplicates.
+ * Sizes: n, m >= 1, 0 <= m_eq <= m, nnz < 2^31, n, m < 2^31. */
+typedef struct pdhg_problem {
+  int64_t n, m, m_eq, nnz;
+  const int64_t *row_ptr; /* device [m+1] */
+  const int32_t *col;     /* device [nnz] */
+  const double *val;      /* device [nnz] */
+  const double *c;        /* device [n]   */
+  const double *l;        /* device [n]   */
+  const double *u;        /* device [n]   */
+  const double *q;        /* device [m]   */
+} pdhg_problem;
+
+/* Options.  pdhg_opts_default fills the values listed in the comments. */
+typedef struct pdhg_opts {
+  double tol;               /* target rel_kkt (1e-8)                                  */
+  int32_t precision;        /* PDHG_PREC_FP64 / PDHG_PREC_MIXED (FP64)                */
+  int32_t check_every;      /* attempts between KKT checks; fixed at 64               */
+  int64_t max_iters;        /* cap on step attempts, all refinement rounds (10^7)     */
+  double time_limit_s;      /* wall limit on the device clock (600)                   */
+  double beta_sufficient;   /* restart if KKT_w(cand) <= 0.2 KKT_w(last restart)      */
+  double beta_necessary;    /* ... or <= 0.8 and increased since the last check       */
+  double beta_artificial;   /* ... or attempts since restart >= 0.36 of all attempts  */
+  double omega_smoothing;   /* primal weight smoothing theta (0.5)                    */
+  double step_reduction_exp; /* eta' = min((1-(k+1)^-0.3) eta_max, ...) (0.3)         */
+  double step_growth_exp;    /* ... (1+(k+1)^-0.6) eta) (0.6)                         */
+  int32_t ruiz_iters;       /* Ruiz l_inf passes (10)                                 */
+  int32_t pock_chambolle;   /* 1: one Pock-Chambolle alpha=1 pass (1)                 */
+  double ir_first_tol;      /* mixed: rel_kkt target of the first FP32 round (1e-4)   */
+  double ir_reduction;      /* mixed: per-round reduction of rel_kkt (0.1)            */
+  int32_t ir_max_rounds;    /* mixed: refinement rounds after the first (100)         */
+  int32_t trace;            /* 1: record per-attempt/per-check trace (testing) (0)    */
+  double fixed_eta;         /* > 0: constant steps eta/omega, no restarts (0)         */
+  double fixed_omega;       /* primal weight in fixed-step mode                       */
+  int32_t bound_obj_rescale; /* 1: also scale q, l, u by 1/(1+||q~||) and c by
+                                1/(1+||c~||) after Ruiz + Pock-Chambolle (0)          */
+  int32_t artificial_total; /* 1: the artificial restart compares with the attempts of
+                               all refinement rounds, not the current round's (1)     */
+  int32_t host_loop;        /* 1: launch each 64-attempt body from the host and read the
+                               done flag after every check instead of one CUDA graph
+                               with a device-side while loop (for profilers) (0)      */
+  volatile int32_t *cancel_flag; /* host-mapped int polled at every check, or NULL    */
+} pdhg_opts;
+
+/* Outcome of one solve (host struct written by the library). */
+typedef struct pdhg_result {
+  int32_t status;      /* PDHG_STATUS_*                                     */
+  int32_t ir_rounds;   /* refinement rounds done (mixed), 0 for FP64          */
+  int64_t iterations;  /* step attempts, all rounds                          */
+  int64_t accepted;    /* accepted steps                                     */
+  int64_t restarts;
+  int64_t checks;
+  double rel_p, rel_d, rel_gap, rel_kkt; /* of the returned point, unscaled   */
+  double primal_obj, dual_obj;
+  double solve_seconds;        /* device time of the whole call                */
+  double time_to_tol[3];       /* seconds to rel_kkt <= 1e-4, 1e-6, 1e-8 or -1 */
+  int64_t iters_to_tol[3];     /* attempts to the same                         */
+  double eta, omega;           /* final step size and primal weight            */
+  int64_t kernel_launches;     /* kernels this call ran (graph bodies counted
+                                  once per executed body)                      */
+} pdhg_result;
+
+/* Fill *o with the defaults listed above. */
+int pdhg_opts_default(pdhg_opts *o);
+
+/* Create a workspace for `prob`.  Copies the sparsity structure to the host
+ * once to build the internal row/column orderings and sliced-ELL layouts,
+ * then allocates every device buffer a solve needs.  Values (val, c, l, u, q)
+ * are read at each solve, so they may change between solves; the structure
+ * and the pointers must stay valid and unchanged for the workspace's life.
+ * `opts` may be NULL (defaults).  Synchronises `stream`. */
+int pdhg_workspace_create(const pdhg_problem *prob, const pdhg_opts *opts, void **ws, void *stream);
+
+/* Release a workspace (NULL is ignored). */
+void pdhg_workspace_destroy(void *ws);
+
+/* Replace the options of an existing workspace (validated; no reallocation
+ * except for the trace buffer). */
+int pdhg_set_opts(void *ws, const pdhg_opts *opts);
+
+/* Solve the LP (PDHG with Ruiz + Pock-Chambolle rescaling, adaptive steps,
+ * primal-weight updates, restarts and KKT termination; mixed precision adds
+ * FP64 iterative refinement).  Writes the unscaled solution to x_out [n] and
+ * y_out [m] (device, may be NULL) and the outcome to *res (host).  The whole
+ * PDHG loop runs as one CUDA graph with a device-side while condition; the
+ * host waits once per refinement round. */
+int pdhg_solve(void *ws, double *x_out, double *y_out, pdhg_result *res, void *stream);
+
+/* Solve B LPs that share K, c and q and differ only in their bounds
+ * (branch-and-bound nodes fixing commitments).  l_b, u_b: device [B][n];
+ * x_out: device [B][n], y_out: device [B][m] (may be NULL); res_b: host [B].
+ * Per-instance step size, primal weight, restarts and termination. */
+int pdhg_solve_batched(void *ws, int32_t B, const double *l_b, const double *u_b, double *x_out,
+                       double *y_out, pdhg_result *res_b, void *stream);
+
+/* Vector-Jacobian product of the last pdhg_solve of this workspace:
+ *   given the cotangent g_cost of the optimal cost and g_x [n] of the primal
+ *   solution (device, may be NULL), writes grad_q [m] and grad_c [n] (device)
+ *   = d(g_cost * cost + g_x^T x*)/d(q, c), by implicit differentiation of the
+ *   KKT system on the detected active set. */
+int pdhg_backward(void *ws, double g_cost, const double *g_x, double *grad_q, double *grad_c,
+                  void *stream);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *pdhg_last_error(void);
+
+/* ---- diagnostics (kernel-level tests and measurement) -------------------- */
+
+/* Load the values and run the rescaling of a solve without iterating. */
+int pdhg_prepare(void *ws, void *stream);
+
+/* Row and column scaling factors Dr [m], Dc [n] (device, FP64, original
+ * order): K~ = diag(Dr) K diag(Dc).  Valid after pdhg_prepare or a solve. */
+int pdhg_get_scaling(void *ws, double *Dr, double *Dc, void *stream);
+
+/* out = K~ in (transpose = 0; in [n], out [m]) or K~^T in (transpose = 1;
+ * in [m], out [n]) with the rescaled matrix in the workspace's sliced-ELL
+ * layout, original index order, device FP64 vectors.  precision selects the
+ * FP64 or the FP32 copy of the values (FP32 rounds `in` to float first and
+ * accumulates in FP32). */
+int pdhg_apply_K(void *ws, int32_t transpose, int32_t precision, const double *in, double *out,
+                 void *stream);
+
+/* Copy the trace of the last solve (opts.trace = 1) to host arrays:
+ *   attempts [cap_a][5]: eta, omega, accepted, eta_max, eta_next
+ *   checks   [cap_c][8]: attempts, restart, to_average, omega_after, KKT_w of the
+ *                       current and average iterate, rel_kkt of the current and average
+ * *n_a, *n_c receive the counts recorded (may exceed the caps). */
+int pdhg_get_trace(void *ws, double *attempts, int64_t cap_a, double *checks, int64_t cap_c,
+                   int64_t *n_a, int64_t *n_c);
+
+/* Launch the two per-attempt kernels of `precision` `reps` times each on
+ * `stream` against the workspace's current state, timing each kernel with CUDA
+ * events on that stream; writes the average milliseconds per launch and the
+ * algorithmic bytes per launch of the dual (K x) and adjoint (K^T y) kernels. */
+int pdhg_time_kernels(void *ws, int32_t precision, int32_t reps, double *ms_dual, double *ms_adj,
+                      double *bytes_dual, double *bytes_adj, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDHG_H */

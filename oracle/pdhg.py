@@ -77,6 +77,10 @@ class PDHGResult:
     Dc: np.ndarray
     attempt_log: list = field(default_factory=list)  # (eta, omega, accepted, eta_max)
     check_log: list = field(default_factory=list)    # dict per check
+    x_cur: np.ndarray | None = None   # unscaled current iterate at exit
+    y_cur: np.ndarray | None = None
+    x_avg: np.ndarray | None = None   # unscaled average since the last restart at exit
+    y_avg: np.ndarray | None = None
 
 
 def _kkt_omega(slp: LP, Dr, Dc, lp: LP, x_s, y_s, omega):
@@ -229,7 +233,9 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
     if final is None:
         final = (x, y, kkt(lp, Dc * x, Dr * y))
     xs, ys, res = final
+    xb, yb = (xsum / wsum, ysum / wsum) if wsum > 0 else (x, y)
     return PDHGResult(x=Dc * xs, y=Dr * ys, x_scaled=xs, y_scaled=ys, status=status, attempts=k,
                       accepted=accepted, restarts=restarts, rel_kkt=res.rel_kkt, primal_obj=res.primal_obj,
                       dual_obj=res.dual_obj, eta=eta, omega=omega, Dr=Dr, Dc=Dc,
-                      attempt_log=attempt_log, check_log=check_log)
+                      attempt_log=attempt_log, check_log=check_log, x_cur=Dc * x, y_cur=Dr * y,
+                      x_avg=Dc * xb, y_avg=Dr * yb)

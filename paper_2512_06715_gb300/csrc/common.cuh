@@ -1,0 +1,204 @@
+// Shared device-side definitions of the GB300 PDHG solver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "../../include/pdhg.h"
+
+namespace ucpdhg {
+
+constexpr int kSlice = 32;       // rows per sliced-ELL slice (one warp, one row per lane)
+constexpr int kBlock = 256;      // threads per block of every streaming kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kCheckEvery = 64;  // step attempts between KKT checks (one graph body)
+constexpr int kMaxBlocks = 8192; // upper bound of the persistent grid sizes
+constexpr int kRowSums = 4;      // per-candidate sums of the row-side KKT kernel
+constexpr int kColSums = 5;      // per-candidate sums of the column-side KKT kernel
+
+// Sliced ELL with 32-row slices over the internal (length-sorted) row order.
+// Entry k of row r = 32 s + lane sits at off[s] + 32 k + lane, so the warp
+// owning a slice reads each k-column with one coalesced 128 B / 256 B access.
+// Padding entries carry col = 0 and value 0.
+template <class T>
+struct SellView {
+  const int32_t* off;  // [nslices + 1] element offsets (multiples of 32)
+  const int32_t* col;  // [nnz_pad] internal column index
+  const T* val;        // [nnz_pad]
+  int32_t nslices;
+  int32_t rows;        // logical rows (<= 32 * nslices)
+};
+
+// Device-resident solver state: every scalar decision of the PDHG loop lives
+// here, so the loop never waits on the host.
+struct DevState {
+  // step control
+  double eta, omega;
+  double dx2;        // ||x' - x||^2 of the pending candidate
+  double w_last;     // eta of the last attempt if accepted, else 0
+  double pending_w;  // weight of the y-average update not yet applied
+  double wsum;       // sum of average weights since the last restart
+  double avg_div;    // wsum frozen for restart_apply
+  int32_t par;       // parity of the current iterate buffers
+  int32_t accepted_last;
+  int64_t k;              // attempts this round
+  int64_t since_restart;  // attempts since the last restart
+  int64_t accepted;       // accepted attempts this round
+  int64_t restarts;       // this round
+  int64_t checks;         // this round
+  // restart control
+  double kkt0, kkt_prev;
+  int32_t restart_now, restart_to_avg;
+  // outcome of the last check (best candidate)
+  int32_t done, status;  // status: 0 running/round target met, else PDHG_STATUS_*
+  int32_t best_is_avg, numeric;
+  double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
+  // targets and limits
+  double tol, round_target;
+  int64_t max_k, max_checks;
+  uint64_t t_start, t_limit_ns;
+  double t_tol[3];
+  int64_t k_tol[3];
+  int64_t k_offset;  // attempts of earlier refinement rounds
+  // constants of the method
+  double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
+  int32_t fixed;     // constant steps, no restarts
+  int32_t art_total; // artificial restart against attempts of all rounds
+  int32_t trace_on;
+  int64_t trace_cap_a, trace_cap_c, n_trace_a, n_trace_c;
+  // refinement-round best point (mixed mode): snapshot + stall detection
+  double round_best;
+  int64_t checks_since_best;
+  int64_t stall_min_checks;  // 0 disables the stall rule (plain FP64 solves)
+  int32_t save_best, save_avg;
+  double save_div;
+  // norms of the unscaled data and refinement scalars
+  double qnorm, cnorm;
+  double inv_dp, inv_dd;      // 1/Delta_P, 1/Delta_D
+  double const_p, const_d;    // c~^T x*, q~^T y*
+  // last-block counters of the reducing kernels
+  uint32_t counter;
+  uint32_t counter2;
+};
+
+// Pointers of one precision's iteration.
+template <class T>
+struct IterArgs {
+  SellView<T> K, KT;
+  T* x[2];
+  T* y[2];
+  T* Kx[2];
+  T* KTy[2];
+  T* xbar;  // weighted sums (not divided)
+  T* ybar;
+  T* xa;    // anchors (last restart point)
+  T* ya;
+  T* xs;    // snapshot of the round's best point (mixed mode)
+  T* ys;
+  const T* c;
+  const T* l;
+  const T* u;
+  const T* q;
+  const T* ylo;  // nullptr: -inf on equality rows, 0 on >= rows
+  int32_t n, m, m_eq;
+  DevState* st;
+  double* partials;
+  double* trace_a;  // [cap][5]
+  double* trace_c;  // [cap][6]
+  volatile int32_t* cancel;
+  unsigned long long cond;  // cudaGraphConditionalHandle
+  int32_t in_graph;
+  // FP64 data of the KKT evaluation
+  SellView<double> K64, KT64;
+  const double* q_res;  // q^ (FP64)
+  const double* c_res;  // c^ (FP64)
+  const double* q_obj;  // q~
+  const double* c_obj;  // c~
+  const double* l_obj;  // l~
+  const double* u_obj;  // u~
+  const double* Dr;
+  const double* Dc;
+  double* Kz_avg;   // [m] K~ xbar / wsum (FP64)
+  double* KTz_avg;  // [n] K~^T ybar / wsum (FP64)
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of NV values per thread; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* [kWarps*NV] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[wid * NV + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < kWarps; ++w) s += smem[w * NV + k];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Writes this block's NV partial sums and returns true in every thread of the
+// block that finished last.  That block then reads all partials with
+// final_sum (fixed order, so the result does not depend on scheduling).
+template <int NV>
+__device__ __forceinline__ bool publish_partials(double (&v)[NV], double* partials,
+                                                 uint32_t* counter) {
+  __shared__ double smem[kWarps * NV];
+  __shared__ int last;
+  block_sum<NV>(v, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[(size_t)blockIdx.x * NV + k] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last != 0;
+}
+
+// Fixed-order sum over the partials of `nblocks` blocks; valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void final_sum(const double* partials, int nblocks, double (&out)[NV]) {
+  __shared__ double smem[kWarps * NV];
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __ldcg(partials + (size_t)b * NV + k);
+  block_sum<NV>(v, smem);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = v[k];
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <class T>
+__device__ __forceinline__ T dual_floor(const T* ylo, int i, int m_eq) {
+  if (ylo) return ylo[i];
+  return (i < m_eq) ? (T)(-INFINITY) : (T)0;
+}
+
+// ---- host-side launchers (defined in the .cu files) ----------------------------
+struct Workspace;
+
+}  // namespace ucpdhg

@@ -1,0 +1,349 @@
+// The two kernels of one PDHG step attempt (Sec. II.E iteration, PDLP form):
+//
+//   k_dual    : K x' (sliced ELL SpMV, warp per 32-row slice) fused with the
+//               projected dual step y' = max(y_lo, y + sigma (q - 2 K x' + K x)),
+//               the lazy y-average update, and the FP64 partial sums ||dy||^2 and
+//               dy^T K dx.  The block that finishes last reduces the partials in
+//               fixed order and takes the adaptive step decision (accept/reject,
+//               next eta) on the device.
+//   k_adjoint : K^T y' for an accepted step (else the cached K^T y), the
+//               x-average update, and -- fused -- the primal step of the NEXT
+//               attempt x'' = proj_[l,u](x - tau (c - K^T y)) with ||dx||^2.
+//
+// Buffers are double-buffered by a parity bit in the device state: the
+// current iterate is buf[par], the candidate buf[1-par]; accepting flips par.
+#include "internal.cuh"
+
+namespace ucpdhg {
+
+// Row dot product of one sliced-ELL row (lane of slice s) with x.  Entries
+// are consumed in predicated chunks of 4 so that all column/value loads of a
+// short row (UC rows have 2-25 entries) are in flight together before the
+// dependent gathers of x.
+template <class T>
+__device__ __forceinline__ T sell_dot(const SellView<T>& A, int s, int lane, const T* __restrict__ x) {
+  const int o0 = __ldg(A.off + s);
+  const int w = (__ldg(A.off + s + 1) - o0) >> 5;
+  const int32_t* cp = A.col + o0 + lane;
+  const T* vp = A.val + o0 + lane;
+  T acc = 0;
+  for (int k0 = 0; k0 < w; k0 += 4) {
+    int c[4];
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool ok = k0 + u < w;
+      c[u] = ok ? __ldg(cp + (k0 + u) * kSlice) : 0;
+      v[u] = ok ? __ldg(vp + (k0 + u) * kSlice) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k0 + u < w) acc += v[u] * __ldg(x + c[u]);
+  }
+  return acc;
+}
+
+// Adaptive step rule on the device (thread 0 of the last block of k_dual).
+template <class T>
+__device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, double inter) {
+  const double eta = st->eta, omega = st->omega;
+  const double movement = omega * st->dx2 + dy2 / omega;
+  const double interaction = 2.0 * fabs(inter);
+  const double eta_max = interaction > 0.0 ? movement / interaction : INFINITY;
+  const int64_t k = st->k + 1;
+  st->k = k;
+  double eta_next = fmin((1.0 - pow((double)(k + 1), -st->red_exp)) * eta_max,
+                         (1.0 + pow((double)(k + 1), -st->grow_exp)) * eta);
+  int accept = eta <= eta_max;
+  if (st->fixed) {
+    accept = 1;
+    eta_next = eta;
+  }
+  if (st->trace_on && a.trace_a) {
+    int64_t t = st->n_trace_a;
+    if (t < st->trace_cap_a) {
+      double* r = a.trace_a + t * 5;
+      r[0] = eta;
+      r[1] = omega;
+      r[2] = (double)accept;
+      r[3] = eta_max;
+      r[4] = eta_next;
+    }
+    st->n_trace_a = t + 1;
+  }
+  if (accept) {
+    st->par = 1 - st->par;
+    st->w_last = eta;
+    st->pending_w = eta;
+    st->wsum += eta;
+    st->accepted += 1;
+  } else {
+    st->w_last = 0.0;
+    st->pending_w = 0.0;
+  }
+  st->accepted_last = accept;
+  st->since_restart += 1;
+  st->eta = eta_next;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  const int p = st->par;
+  const double pw = st->pending_w;
+  const T sigma = (T)(st->eta * st->omega);
+  const T* __restrict__ xn = a.x[1 - p];
+  const T* __restrict__ yc = a.y[p];
+  const T* __restrict__ kxc = a.Kx[p];
+  T* __restrict__ yn = a.y[1 - p];
+  T* __restrict__ kxn = a.Kx[1 - p];
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  double acc[2] = {0.0, 0.0};
+  for (int s = gw; s < a.K.nslices; s += nw) {
+    const int i = s * kSlice + lane;
+    const bool valid = i < a.m;
+    // row operands do not depend on the product: load them first so their
+    // latency overlaps the matrix stream
+    T ko = 0, yo = 0, qi = 0, lo = 0, yb = 0;
+    if (valid) {
+      ko = kxc[i];
+      yo = yc[i];
+      qi = a.q[i];
+      if (i >= a.m_eq) lo = dual_floor(a.ylo, i, a.m_eq);
+      if (pw != 0.0) yb = a.ybar[i];
+    }
+    const T kx = sell_dot(a.K, s, lane, xn);
+    if (valid) {
+      T t = qi - (T)2 * kx;
+      t = t + ko;
+      T v = yo + sigma * t;
+      if (i >= a.m_eq) v = max(v, lo);
+      kxn[i] = kx;
+      yn[i] = v;
+      if (pw != 0.0) a.ybar[i] = yb + (T)pw * yo;
+      const double dy = (double)v - (double)yo;
+      const double dk = (double)kx - (double)ko;
+      acc[0] += dy * dy;
+      acc[1] += dy * dk;
+    }
+  }
+  if (publish_partials<2>(acc, a.partials, &st->counter)) {
+    double tot[2];
+    final_sum<2>(a.partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      decide_step(st, a, tot[0], tot[1]);
+      st->counter = 0;
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock, 6) k_adjoint(IterArgs<T> a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  const int p = st->par;
+  const int acc_last = st->accepted_last;
+  const double wl = st->w_last;
+  const T tau = (T)(st->eta / st->omega);
+  const T* __restrict__ yc = a.y[p];
+  const T* __restrict__ xc = a.x[p];
+  T* __restrict__ kty = a.KTy[p];
+  T* __restrict__ xn = a.x[1 - p];
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  double acc[1] = {0.0};
+  for (int s = gw; s < a.KT.nslices; s += nw) {
+    const int j = s * kSlice + lane;
+    const bool valid = j < a.n;
+    T x0 = 0, cj = 0, lj = 0, uj = 0, xb = 0, g = 0;
+    if (valid) {
+      x0 = xc[j];
+      cj = a.c[j];
+      lj = a.l[j];
+      uj = a.u[j];
+      if (acc_last && wl != 0.0) xb = a.xbar[j];
+      if (!acc_last) g = kty[j];
+    }
+    if (acc_last) g = sell_dot(a.KT, s, lane, yc);
+    if (valid) {
+      if (acc_last) kty[j] = g;
+      if (acc_last && wl != 0.0) a.xbar[j] = xb + (T)wl * x0;
+      T v = x0 - tau * (cj - g);
+      v = min(max(v, lj), uj);
+      xn[j] = v;
+      const double d = (double)v - (double)x0;
+      acc[0] += d * d;
+    }
+  }
+  if (publish_partials<1>(acc, a.partials, &st->counter)) {
+    double tot[1];
+    final_sum<1>(a.partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      st->dx2 = tot[0];
+      st->counter = 0;
+    }
+  }
+}
+
+// x = proj_[l,u](0), y = proj(0), averages and anchors reset; K x and K^T y.
+template <class T>
+__global__ void k_init_vectors(IterArgs<T> a) {
+  const int64_t N = a.n > a.m ? a.n : a.m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < a.n) {
+      T v = min(max((T)0, a.l[t]), a.u[t]);
+      a.x[0][t] = v;
+      a.x[1][t] = v;
+      a.xa[t] = v;
+      a.xbar[t] = 0;
+    }
+    if (t < a.m) {
+      T v = 0;
+      if ((int)t >= a.m_eq) v = max(v, dual_floor(a.ylo, (int)t, a.m_eq));
+      a.y[0][t] = v;
+      a.y[1][t] = v;
+      a.ya[t] = v;
+      a.ybar[t] = 0;
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_spmv_into(SellView<T> A, const T* __restrict__ x,
+                                                      T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  for (int s = gw; s < A.nslices; s += nw) {
+    const T v = sell_dot(A, s, lane, x);
+    const int r = s * kSlice + lane;
+    if (r < A.rows) y[r] = v;
+  }
+}
+
+__global__ void k_state_init(DevState* st, RoundInit r, const double* scalars) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (r.reset_steps) {
+    st->eta = r.eta > 0.0 ? r.eta : scalars[0];
+    st->omega = r.omega > 0.0 ? r.omega : scalars[1];
+  }
+  st->dx2 = 0.0;
+  st->w_last = 0.0;
+  st->pending_w = 0.0;
+  st->wsum = 0.0;
+  st->avg_div = 0.0;
+  st->par = 0;
+  st->accepted_last = 0;
+  st->k = 0;
+  st->since_restart = 0;
+  st->accepted = 0;
+  st->restarts = 0;
+  st->checks = 0;
+  st->kkt0 = 0.0;
+  st->kkt_prev = 0.0;
+  st->restart_now = 0;
+  st->restart_to_avg = 0;
+  st->done = 0;
+  st->status = 0;
+  st->best_is_avg = 0;
+  st->numeric = 0;
+  st->tol = r.tol;
+  st->round_target = r.round_target;
+  st->max_k = r.max_k;
+  st->max_checks = r.max_checks;
+  st->k_offset = r.k_offset;
+  st->t_limit_ns = r.t_limit_ns;
+  if (r.first_round) {
+    st->t_start = globaltimer_ns();
+    for (int i = 0; i < 3; ++i) {
+      st->t_tol[i] = -1.0;
+      st->k_tol[i] = -1;
+    }
+    st->n_trace_a = 0;
+    st->n_trace_c = 0;
+  }
+  st->beta_suff = r.beta_suff;
+  st->beta_nec = r.beta_nec;
+  st->beta_art = r.beta_art;
+  st->omega_smooth = r.omega_smooth;
+  st->red_exp = r.red_exp;
+  st->grow_exp = r.grow_exp;
+  st->fixed = r.fixed;
+  st->art_total = r.art_total;
+  st->trace_on = r.trace_on;
+  st->trace_cap_a = r.trace_cap_a;
+  st->trace_cap_c = r.trace_cap_c;
+  st->qnorm = scalars[2];
+  st->cnorm = scalars[3];
+  st->inv_dp = r.inv_dp;
+  st->inv_dd = r.inv_dd;
+  st->const_p = scalars[6];
+  st->const_d = scalars[7];
+  st->round_best = INFINITY;
+  st->checks_since_best = 0;
+  st->stall_min_checks = r.stall_min_checks;
+  st->save_best = 0;
+  st->save_avg = 0;
+  st->counter = 0;
+  st->counter2 = 0;
+}
+
+// ---------------------------------------------------------------------------
+
+static int vgrid(int64_t n) {
+  int64_t g = (n + kBlock - 1) / kBlock;
+  if (g > 152 * 8) g = 152 * 8;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <class T>
+void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
+  (void)grid;
+  k_init_vectors<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a);
+  int gk = (a.K.nslices + kWarps - 1) / kWarps;
+  int gt = (a.KT.nslices + kWarps - 1) / kWarps;
+  if (gk > kMaxBlocks) gk = kMaxBlocks;
+  if (gt > kMaxBlocks) gt = kMaxBlocks;
+  k_spmv_into<T><<<gk < 1 ? 1 : gk, kBlock, 0, s>>>(a.K, a.x[0], a.Kx[0]);
+  k_spmv_into<T><<<gt < 1 ? 1 : gt, kBlock, 0, s>>>(a.KT, a.y[0], a.KTy[0]);
+}
+
+template <class T>
+void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s) {
+  k_dual<T><<<grid, kBlock, 0, s>>>(a);
+}
+
+template <class T>
+void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s) {
+  k_adjoint<T><<<grid, kBlock, 0, s>>>(a);
+}
+
+void launch_state_init(DevState* st, const RoundInit& r, const double* scalars, cudaStream_t s) {
+  k_state_init<<<1, 32, 0, s>>>(st, r, scalars);
+}
+
+int blocks_per_sm_iter() {
+  int best = 1 << 30;
+  const void* fns[4] = {(const void*)&k_dual<double>, (const void*)&k_adjoint<double>,
+                        (const void*)&k_dual<float>, (const void*)&k_adjoint<float>};
+  for (const void* f : fns) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0) != cudaSuccess) b = 4;
+    best = b < best ? b : best;
+  }
+  return best < 1 ? 1 : best;
+}
+
+template void launch_init_iterates<double>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_init_iterates<float>(const IterArgs<float>&, int, cudaStream_t);
+template void launch_dual<double>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_dual<float>(const IterArgs<float>&, int, cudaStream_t);
+template void launch_adjoint<double>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_adjoint<float>(const IterArgs<float>&, int, cudaStream_t);
+
+}  // namespace ucpdhg

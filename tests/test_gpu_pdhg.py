@@ -1,0 +1,186 @@
+"""GPU parity of the PDHG path (through the C ABI) against the CPU oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.lp import kkt, lp_from_arrays, max_violation
+from oracle.pdhg import pdhg_solve
+from oracle.scaling import rescale
+from paper_2512_06715_gb300.instances import build_instance, workload
+from tests.conftest import instance_lp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_06715_gb300 import build
+    build.build()
+
+
+def _ws(inst, **kw):
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    kw.setdefault("time_limit_s", 120.0)
+    return Workspace.from_instance(inst, default_opts(**kw))
+
+
+def _random_lp(m, n, seed, long_rows=()):
+    """Random sparse LP with empty rows, one-entry rows, long rows and a ragged
+    tail (m, n not multiples of 32)."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(m):
+        if i % 17 == 3:
+            k = 0
+        elif i % 5 == 1:
+            k = 1
+        elif i in long_rows:
+            k = min(n, 150)
+        else:
+            k = int(rng.integers(2, 9))
+        cols = np.sort(rng.choice(n, size=k, replace=False))
+        rows.append(cols)
+    row_ptr = np.zeros(m + 1, np.int64)
+    row_ptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32) if row_ptr[-1] else np.zeros(0, np.int32)
+    val = rng.uniform(-3, 3, size=len(col)) * np.exp(rng.uniform(-4, 4, size=len(col)))
+    c = rng.uniform(-1, 1, n)
+    l = np.where(rng.random(n) < 0.3, -np.inf, -rng.uniform(0, 5, n))
+    u = np.where(rng.random(n) < 0.3, np.inf, rng.uniform(0, 5, n))
+    q = rng.uniform(-1, 1, m)
+    return row_ptr, col, val, c, l, u, q
+
+
+@pytest.mark.parametrize("shape", [(1000, 777), (45, 1000), (3001, 2999)])
+def test_spmv_and_scaling_parity(shape):
+    from paper_2512_06715_gb300.pdhg import PREC_FP64, PREC_MIXED, Workspace, default_opts
+    m, n = shape
+    rp, col, val, c, l, u, q = _random_lp(m, n, seed=m + n, long_rows=(7, m - 1))
+    m_eq = m // 3
+    ws = Workspace(rp, col, val, c, l, u, q, m_eq, default_opts())
+    ws.prepare()
+    Dr, Dc = (t.cpu().numpy() for t in ws.scaling())
+    lp = lp_from_arrays(rp, col, val, q, c, l, u, m_eq, n=n)
+    slp, Dr_o, Dc_o = rescale(lp)
+    assert np.allclose(Dr, Dr_o, rtol=1e-12, atol=0)
+    assert np.allclose(Dc, Dc_o, rtol=1e-12, atol=0)
+    K = slp.K
+    rng = np.random.default_rng(1)
+    xv, yv = rng.standard_normal(n), rng.standard_normal(m)
+    kx = ws.apply_K(torch.from_numpy(xv)).cpu().numpy()
+    kty = ws.apply_K(torch.from_numpy(yv), transpose=True).cpu().numpy()
+    scale_r = (abs(K) @ np.abs(xv)) + 1e-300
+    scale_c = (abs(K.T) @ np.abs(yv)) + 1e-300
+    assert np.all(np.abs(kx - K @ xv) <= 1e-14 * scale_r)
+    assert np.all(np.abs(kty - K.T @ yv) <= 1e-14 * scale_c)
+    kx32 = ws.apply_K(torch.from_numpy(xv), precision=PREC_MIXED).cpu().numpy()
+    kty32 = ws.apply_K(torch.from_numpy(yv), transpose=True, precision=PREC_MIXED).cpu().numpy()
+    assert np.all(np.abs(kx32 - K @ xv) <= 2e-6 * scale_r)
+    assert np.all(np.abs(kty32 - K.T @ yv) <= 2e-6 * scale_c)
+    # empty rows give exact zeros
+    empty = np.where(np.diff(rp) == 0)[0]
+    assert np.all(kx[empty] == 0.0)
+    ws.close()
+
+
+def test_fixed_step_iterates_match_oracle(tiny24):
+    """Constant steps, no restarts: iterates after 128 attempts agree with the
+    oracle to 1e-10 relative."""
+    inst, lp = tiny24
+    slp, _, _ = rescale(lp)
+    eta = 0.9 / np.abs(slp.K.data).max()
+    omega = np.linalg.norm(slp.c) / np.linalg.norm(slp.q)
+    ws = _ws(inst, fixed_eta=eta, fixed_omega=omega, max_iters=128, tol=1e-30)
+    x, y, r = ws.solve()
+    x, y = x.cpu().numpy(), y.cpu().numpy()
+    ref = pdhg_solve(lp, fixed=dict(eta=eta, omega=omega), stop_after=128)
+    cands = [(ref.x_cur, ref.y_cur), (ref.x_avg, ref.y_avg)]
+    errs = [max(np.abs(x - a).max() / np.abs(a).max(), np.abs(y - b).max() / np.abs(b).max())
+            for a, b in cands]
+    assert min(errs) <= 1e-10, errs
+    assert r["iterations"] == 128 and r["restarts"] == 0
+
+
+def test_adaptive_schedule_replay(tiny24):
+    """Adaptive steps and restarts: the oracle replays the GPU's recorded
+    schedule for 192 attempts (three checks); iterates agree to 1e-10 relative
+    and the oracle's own decisions equal the GPU's."""
+    inst, lp = tiny24
+    ws = _ws(inst, max_iters=192, tol=1e-30, trace=1)
+    x, y, r = ws.solve()
+    x, y = x.cpu().numpy(), y.cpu().numpy()
+    ta, tc = ws.trace()
+    assert len(ta) == 192 and len(tc) == 3
+    sched = dict(attempts=[(e[0], e[1], int(e[2])) for e in ta],
+                 checks=[(int(c[1]), int(c[2])) for c in tc])
+    ref = pdhg_solve(lp, tol=1e-30, stop_after=192, schedule=sched, record=True)
+    own = np.array([a[5] for a in ref.attempt_log])
+    assert np.array_equal(own, ta[:, 2].astype(int))
+    # eta_max and the next step agree with the oracle's own computation
+    eta_max_o = np.array([a[3] for a in ref.attempt_log])
+    fin = np.isfinite(eta_max_o)
+    assert np.allclose(ta[fin, 3], eta_max_o[fin], rtol=1e-8)
+    for c_gpu, c_or in zip(tc[:-1], ref.check_log[:-1]):
+        assert int(c_gpu[1]) == int(c_or["restart_own"])
+        if int(c_gpu[1]):
+            assert int(c_gpu[2]) == int(c_or["to_avg_own"])
+    cands = [(ref.x_cur, ref.y_cur), (ref.x_avg, ref.y_avg)]
+    errs = [max(np.abs(x - a).max() / np.abs(a).max(), np.abs(y - b).max() / np.abs(b).max())
+            for a, b in cands]
+    assert min(errs) <= 1e-10, errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_tiny_matches_oracle(tiny24, tiny24_oracle, precision):
+    inst, lp = tiny24
+    ws = _ws(inst, precision=precision, tol=1e-8)
+    x, y, r = ws.solve()
+    x, y = x.cpu().numpy(), y.cpu().numpy()
+    assert r["status_name"] == "optimal", r
+    chk = kkt(lp, x, y)
+    assert chk.rel_kkt <= 1.5e-8, chk.rel_kkt
+    assert abs(chk.rel_kkt - r["rel_kkt"]) <= 1e-2 * r["rel_kkt"] + 1e-12
+    ref = tiny24_oracle
+    assert abs(chk.primal_obj - ref.primal_obj) <= 1e-6 * abs(ref.primal_obj)
+    assert max_violation(lp, x) <= 1e-7 * max(1.0, np.abs(lp.q).max())
+    assert r["time_to_tol"][0] > 0 and r["time_to_tol"][2] >= r["time_to_tol"][0]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_solve_small_vs_oracle(seed):
+    inst = build_instance(8, 10, 6, 6, seed=seed)
+    lp = instance_lp(inst)
+    ref = pdhg_solve(lp, tol=1e-9, max_attempts=1_000_000)
+    for prec in ("fp64", "mixed"):
+        ws = _ws(inst, precision=prec, tol=1e-9)
+        x, y, r = ws.solve()
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        assert r["status_name"] == "optimal"
+        assert abs(kkt(lp, x, y).primal_obj - ref.primal_obj) <= 1e-7 * abs(ref.primal_obj)
+
+
+def test_limits_and_cancel(tiny24):
+    inst, lp = tiny24
+    ws = _ws(inst, max_iters=256, tol=1e-12)
+    _, _, r = ws.solve()
+    assert r["status_name"] == "iteration_limit" and r["iterations"] == 256
+    ws.set_opts(max_iters=10_000_000, time_limit_s=0.002)
+    _, _, r = ws.solve()
+    assert r["status_name"] in ("time_limit", "optimal")
+    flag = torch.ones(1, dtype=torch.int32).pin_memory()
+    ws.set_opts(time_limit_s=60.0, cancel_flag=flag.data_ptr())
+    _, _, r = ws.solve()
+    assert r["status_name"] == "cancelled" and r["iterations"] == 64
+
+
+def test_nan_data_reports_numeric():
+    from paper_2512_06715_gb300.pdhg import PDHGError
+    inst = build_instance(6, 8, 6, 6, seed=0)
+    inst.c = inst.c.copy()
+    inst.c[3] = np.nan
+    ws = _ws(inst)
+    with pytest.raises(PDHGError, match="NUMERIC"):
+        ws.solve()
