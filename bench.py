@@ -314,6 +314,7 @@ def run_ours(args):
             "time_to_tolerance": ttt,
             "roofline": roofline,
             "gpu_launches": launches,
+            "kernel_tuning": ws.tuning(),
             "e2e": e2e,
             "clocks": clk,
             "cpu_baseline": cpu,

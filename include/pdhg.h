@@ -105,6 +105,9 @@ typedef struct pdhg_opts {
   int32_t host_loop;        /* 1: launch each 64-attempt body from the host and read the
                                done flag after every check instead of one CUDA graph
                                with a device-side while loop (for profilers) (0)      */
+  int32_t autotune;         /* 1: time the launch variants of the per-attempt kernels
+                               at the first solve of each precision and keep the
+                               fastest; 0: fixed defaults (1)                         */
   volatile int32_t *cancel_flag; /* host-mapped int polled at every check, or NULL    */
 } pdhg_opts;
 
@@ -194,6 +197,11 @@ int pdhg_apply_K(void *ws, int32_t transpose, int32_t precision, const double *i
  * *n_a, *n_c receive the counts recorded (may exceed the caps). */
 int pdhg_get_trace(void *ws, double *attempts, int64_t cap_a, double *checks, int64_t cap_c,
                    int64_t *n_a, int64_t *n_c);
+
+/* Launch configuration chosen for the per-attempt kernels, host int32 [8]:
+ * FP64 {dual unroll, dual grid, adjoint unroll, adjoint grid}, then FP32
+ * (zeros for a precision not yet solved). */
+int pdhg_get_tuning(void *ws, int32_t *cfg);
 
 /* Launch the two per-attempt kernels of `precision` `reps` times each on
  * `stream` against the workspace's current state, timing each kernel with CUDA

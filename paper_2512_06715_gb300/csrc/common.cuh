@@ -120,6 +120,8 @@ struct IterArgs {
   const double* u_obj;  // u~
   const double* Dr;
   const double* Dc;
+  const double* iDr;  // 1 / Dr (the KKT kernels multiply: FP64 division is slow)
+  const double* iDc;  // 1 / Dc
   double* Kz_avg;   // [m] K~ xbar / wsum (FP64)
   double* KTz_avg;  // [n] K~^T ybar / wsum (FP64)
 };

@@ -63,6 +63,13 @@ struct RoundInit {
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
 };
 
+// Launch configuration of the two per-attempt kernels of one precision:
+// slices in flight per warp (unroll) and grid size, picked by timing.
+struct Tune {
+  int unroll_dual = 1, grid_dual = 0, unroll_adj = 1, grid_adj = 0;
+  bool done = false;
+};
+
 struct Workspace {
   int device = 0;
   int num_sms = 0;
@@ -74,6 +81,7 @@ struct Workspace {
   int32_t* perm_col = nullptr;
   // FP64 vectors, internal order
   double *Dr = nullptr, *Dc = nullptr, *fac_r = nullptr, *fac_c = nullptr;
+  double *iDr = nullptr, *iDc = nullptr;
   double *c_s = nullptr, *l_s = nullptr, *u_s = nullptr, *q_s = nullptr;  // rescaled LP
   double *c_h = nullptr, *l_h = nullptr, *u_h = nullptr, *q_h = nullptr, *ylo_h = nullptr;
   float *c_f = nullptr, *l_f = nullptr, *u_f = nullptr, *q_f = nullptr, *ylo_f = nullptr;
@@ -93,6 +101,7 @@ struct Workspace {
   bool values_f32 = false;  // FP32 matrix copy up to date
   bool solved = false;      // x_star/y_star hold a solution
   int grid_k = 0, grid_kt = 0, grid_vec = 0;
+  Tune tune[2];  // [0] FP64, [1] FP32
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -117,9 +126,9 @@ void launch_to_f64(const float* in, double* out, int64_t n, cudaStream_t s);
 template <class T>
 void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s);
 template <class T>
-void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s);
+void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll);
 template <class T>
-void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s);
+void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll);
 void launch_state_init(DevState* st, const RoundInit& r, const double* scalars, cudaStream_t s);
 int blocks_per_sm_iter();  // resident blocks per SM of the per-attempt kernels (both precisions)
 

@@ -101,6 +101,8 @@ IterArgs<T> make_args(Workspace* w) {
   a.u_obj = w->u_s;
   a.Dr = w->Dr;
   a.Dc = w->Dc;
+  a.iDr = w->iDr;
+  a.iDc = w->iDc;
   a.Kz_avg = w->Kz_avg;
   a.KTz_avg = w->KTz_avg;
   return a;
@@ -137,6 +139,89 @@ static int grid_for(Workspace* w, int per_sm, int nslices) {
   return g < 1 ? 1 : g;
 }
 
+__global__ void k_reopen_state(DevState* st) {
+  st->done = 0;
+  st->counter = 0;
+  st->trace_on = 0;
+}
+
+template <class T>
+static void run_dual(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
+  const Tune& t = w->tune[sizeof(T) == 8 ? 0 : 1];
+  launch_dual<T>(a, t.grid_dual, s, t.unroll_dual);
+}
+
+template <class T>
+static void run_adjoint(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
+  const Tune& t = w->tune[sizeof(T) == 8 ? 0 : 1];
+  launch_adjoint<T>(a, t.grid_adj, s, t.unroll_adj);
+}
+
+// Picks, by timing on this workspace's matrix, the slices in flight per warp
+// (1, 2, 4) and the grid size (2 to 8 blocks per SM) of each per-attempt
+// kernel.  The candidate launches run real attempts on scratch state; the
+// caller re-initialises the iterates afterwards.
+template <class T>
+static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  Tune& t = w->tune[pi];
+  if (t.done) return PDHG_OK;
+  t.unroll_dual = t.unroll_adj = 1;
+  t.grid_dual = w->grid_k;
+  t.grid_adj = w->grid_kt;
+  if (!w->opts.autotune) {
+    t.done = true;
+    return PDHG_OK;
+  }
+  const int unrolls[3] = {1, 2, 4};
+  const int bps[5] = {2, 3, 4, 6, 8};
+  for (int which = 0; which < 2; ++which) {
+    const int nsl = which == 0 ? w->K.nslices : w->KT.nslices;
+    float best = 1e30f;
+    int bu = 1, bg = which == 0 ? w->grid_k : w->grid_kt;
+    for (int ui = 0; ui < 3; ++ui) {
+      const int U = unrolls[ui];
+      const int need = (nsl + kWarps * U - 1) / (kWarps * U);
+      for (int bi = 0; bi < 5; ++bi) {
+        int g = std::min(w->num_sms * bps[bi], std::min(need, kMaxBlocks));
+        if (g < 1) g = 1;
+        k_reopen_state<<<1, 1, 0, s>>>(w->st);
+        if (which == 0)
+          launch_dual<T>(a, g, s, U);
+        else
+          launch_adjoint<T>(a, g, s, U);
+        CK(cudaEventRecord(w->ev[2], s));
+        for (int r = 0; r < 3; ++r) {
+          if (which == 0)
+            launch_dual<T>(a, g, s, U);
+          else
+            launch_adjoint<T>(a, g, s, U);
+        }
+        CK(cudaEventRecord(w->ev[3], s));
+        CK(cudaEventSynchronize(w->ev[3]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, w->ev[2], w->ev[3]));
+        if (ms < best * 0.98f) {
+          best = ms;
+          bu = U;
+          bg = g;
+        }
+        if (g == need) break;  // larger grids add nothing
+      }
+    }
+    if (which == 0) {
+      t.unroll_dual = bu;
+      t.grid_dual = bg;
+    } else {
+      t.unroll_adj = bu;
+      t.grid_adj = bg;
+    }
+  }
+  CK(cudaGetLastError());
+  t.done = true;
+  return PDHG_OK;
+}
+
 template <class T>
 static int build_graph(Workspace* w) {
   const int pi = sizeof(T) == 8 ? 0 : 1;
@@ -162,8 +247,8 @@ static int build_graph(Workspace* w) {
   a.in_graph = 1;
   a.cond = (unsigned long long)h;
   for (int k = 0; k < kCheckEvery; ++k) {
-    launch_dual<T>(a, w->grid_k, w->cap_stream);
-    launch_adjoint<T>(a, w->grid_kt, w->cap_stream);
+    run_dual<T>(w, a, w->cap_stream);
+    run_adjoint<T>(w, a, w->cap_stream);
   }
   launch_check<T>(a, w->grid_k, w->grid_kt, 0, w->cap_stream);
   cudaGraph_t captured = nullptr;
@@ -234,7 +319,6 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     if ((rc = alloc_bufs(w, &w->b64)) != PDHG_OK) return rc;
   }
   if ((rc = ensure_trace(w)) != PDHG_OK) return rc;
-  if ((rc = build_graph<T>(w)) != PDHG_OK) return rc;
   const pdhg_opts& o = w->opts;
   CK(cudaEventRecord(w->ev[0], s));
   launch_prepare(w, s);
@@ -298,17 +382,24 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     ri.omega_smooth = o.omega_smoothing;
     ri.red_exp = o.step_reduction_exp;
     ri.grow_exp = o.step_growth_exp;
+    if (r == 0 && !w->tune[mixed ? 1 : 0].done) {
+      launch_state_init(w->st, ri, w->scalars, s);
+      launch_init_iterates<T>(a, 0, s);
+      launch_adjoint<T>(a, w->grid_kt, s, 1);
+      if ((rc = autotune<T>(w, a, s)) != PDHG_OK) return rc;
+    }
+    if (!o.host_loop && (rc = build_graph<T>(w)) != PDHG_OK) return rc;
     launch_state_init(w->st, ri, w->scalars, s);
     launch_init_iterates<T>(a, 0, s);
-    launch_adjoint<T>(a, w->grid_kt, s);
+    run_adjoint<T>(w, a, s);
     launch_check<T>(a, w->grid_k, w->grid_kt, 1, s);
     if (o.host_loop) {
       // Same kernels as the graph body, launched from the host; the done flag
       // is read after every check (one host wait per 64 attempts).
       for (;;) {
         for (int k = 0; k < kCheckEvery; ++k) {
-          launch_dual<T>(a, w->grid_k, s);
-          launch_adjoint<T>(a, w->grid_kt, s);
+          run_dual<T>(w, a, s);
+          run_adjoint<T>(w, a, s);
         }
         launch_check<T>(a, w->grid_k, w->grid_kt, 0, s);
         CK(cudaMemcpyAsync(w->st_host, w->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -406,6 +497,7 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->bound_obj_rescale = 0;
   o->artificial_total = 1;
   o->host_loop = 0;
+  o->autotune = 1;
   o->cancel_flag = nullptr;
   return PDHG_OK;
 }
@@ -495,6 +587,8 @@ extern "C" int pdhg_workspace_create(const pdhg_problem* prob, const pdhg_opts* 
     A(&w->Dc, n);
     A(&w->fac_r, m);
     A(&w->fac_c, n);
+    A(&w->iDr, m);
+    A(&w->iDc, n);
     A(&w->c_s, n);
     A(&w->l_s, n);
     A(&w->u_s, n);
@@ -661,10 +755,18 @@ extern "C" int pdhg_get_trace(void* ws, double* attempts, int64_t cap_a, double*
   return PDHG_OK;
 }
 
-__global__ void k_reopen_state(DevState* st) {
-  st->done = 0;
-  st->counter = 0;
-  st->trace_on = 0;
+extern "C" int pdhg_get_tuning(void* ws, int32_t* cfg) {
+  g_err.clear();
+  if (!ws || !cfg) return fail(PDHG_ERR_INVALID_ARG, "NULL argument");
+  Workspace* w = (Workspace*)ws;
+  for (int p = 0; p < 2; ++p) {
+    const Tune& t = w->tune[p];
+    cfg[4 * p + 0] = t.done ? t.unroll_dual : 0;
+    cfg[4 * p + 1] = t.done ? t.grid_dual : 0;
+    cfg[4 * p + 2] = t.done ? t.unroll_adj : 0;
+    cfg[4 * p + 3] = t.done ? t.grid_adj : 0;
+  }
+  return PDHG_OK;
 }
 
 extern "C" int pdhg_time_kernels(void* ws, int32_t precision, int32_t reps, double* ms_dual,
@@ -682,21 +784,21 @@ extern "C" int pdhg_time_kernels(void* ws, int32_t precision, int32_t reps, doub
   float t_d = 0.f, t_a = 0.f;
   if (f32) {
     IterArgs<float> a = make_args<float>(w);
-    launch_dual<float>(a, w->grid_k, s);
-    launch_adjoint<float>(a, w->grid_kt, s);
+    run_dual<float>(w, a, s);
+    run_adjoint<float>(w, a, s);
     CK(cudaEventRecord(w->ev[0], s));
-    for (int r = 0; r < reps; ++r) launch_dual<float>(a, w->grid_k, s);
+    for (int r = 0; r < reps; ++r) run_dual<float>(w, a, s);
     CK(cudaEventRecord(w->ev[1], s));
-    for (int r = 0; r < reps; ++r) launch_adjoint<float>(a, w->grid_kt, s);
+    for (int r = 0; r < reps; ++r) run_adjoint<float>(w, a, s);
     CK(cudaEventRecord(w->ev[2], s));
   } else {
     IterArgs<double> a = make_args<double>(w);
-    launch_dual<double>(a, w->grid_k, s);
-    launch_adjoint<double>(a, w->grid_kt, s);
+    run_dual<double>(w, a, s);
+    run_adjoint<double>(w, a, s);
     CK(cudaEventRecord(w->ev[0], s));
-    for (int r = 0; r < reps; ++r) launch_dual<double>(a, w->grid_k, s);
+    for (int r = 0; r < reps; ++r) run_dual<double>(w, a, s);
     CK(cudaEventRecord(w->ev[1], s));
-    for (int r = 0; r < reps; ++r) launch_adjoint<double>(a, w->grid_kt, s);
+    for (int r = 0; r < reps; ++r) run_adjoint<double>(w, a, s);
     CK(cudaEventRecord(w->ev[2], s));
   }
   CK(cudaEventSynchronize(w->ev[2]));

@@ -16,31 +16,64 @@
 
 namespace ucpdhg {
 
-// Row dot product of one sliced-ELL row (lane of slice s) with x.  Entries
-// are consumed in predicated chunks of 4 so that all column/value loads of a
-// short row (UC rows have 2-25 entries) are in flight together before the
-// dependent gathers of x.
+// Row dot products of U consecutive slices (lane = row within each slice)
+// with x.  Entries are consumed in predicated chunks of 4 per slice, so every
+// column/value load of the U short rows (UC rows have 2-25 entries) is in
+// flight before the dependent gathers of x.  U > 1 raises the bytes in flight
+// per warp; the autotuner picks U per matrix.
+// Slice offsets off[s0 .. s0+U] (clamped past the end, giving empty slices).
+// The per-attempt kernels load the NEXT group's offsets one iteration ahead,
+// so this L2 round trip is off the critical path.
+template <class T, int U>
+__device__ __forceinline__ void slice_offsets(const SellView<T>& A, int s0, int (&ob)[U + 1]) {
+#pragma unroll
+  for (int u = 0; u <= U; ++u) ob[u] = __ldg(A.off + min(s0 + u, A.nslices));
+}
+
+template <class T, int U>
+__device__ __forceinline__ void sell_dot_pre(const SellView<T>& A, const int (&ob)[U + 1], int lane,
+                                             const T* __restrict__ x, T (&acc)[U]) {
+  int o0[U], w[U];
+  int wmax = 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    o0[u] = ob[u] + lane;
+    w[u] = (ob[u + 1] - ob[u]) >> 5;
+    wmax = max(wmax, w[u]);
+    acc[u] = 0;
+  }
+  for (int k0 = 0; k0 < wmax; k0 += 4) {
+    int c[U][4];
+    T v[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool ok = k0 + e < w[u];
+        c[u][e] = ok ? __ldg(A.col + o0[u] + (k0 + e) * kSlice) : 0;
+        v[u][e] = ok ? __ldg(A.val + o0[u] + (k0 + e) * kSlice) : (T)0;
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (k0 + e < w[u]) acc[u] += v[u][e] * __ldg(x + c[u][e]);
+  }
+}
+
+template <class T, int U>
+__device__ __forceinline__ void sell_dot_multi(const SellView<T>& A, int s0, int lane,
+                                               const T* __restrict__ x, T (&acc)[U]) {
+  int ob[U + 1];
+  slice_offsets<T, U>(A, s0, ob);
+  sell_dot_pre<T, U>(A, ob, lane, x, acc);
+}
+
 template <class T>
 __device__ __forceinline__ T sell_dot(const SellView<T>& A, int s, int lane, const T* __restrict__ x) {
-  const int o0 = __ldg(A.off + s);
-  const int w = (__ldg(A.off + s + 1) - o0) >> 5;
-  const int32_t* cp = A.col + o0 + lane;
-  const T* vp = A.val + o0 + lane;
-  T acc = 0;
-  for (int k0 = 0; k0 < w; k0 += 4) {
-    int c[4];
-    T v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool ok = k0 + u < w;
-      c[u] = ok ? __ldg(cp + (k0 + u) * kSlice) : 0;
-      v[u] = ok ? __ldg(vp + (k0 + u) * kSlice) : (T)0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (k0 + u < w) acc += v[u] * __ldg(x + c[u]);
-  }
-  return acc;
+  T acc[1];
+  sell_dot_multi<T, 1>(A, s, lane, x, acc);
+  return acc[0];
 }
 
 // Adaptive step rule on the device (thread 0 of the last block of k_dual).
@@ -86,12 +119,15 @@ __device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, doub
   st->eta = eta_next;
 }
 
-template <class T>
+template <class T, int U>
 __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
   const double pw = st->pending_w;
+  // scalars converted once: a per-row FP64 compare or cast costs an FP64-pipe slot
+  const bool has_pw = pw != 0.0;
+  const T pwT = (T)pw;
   const T sigma = (T)(st->eta * st->omega);
   const T* __restrict__ xn = a.x[1 - p];
   const T* __restrict__ yc = a.y[p];
@@ -101,35 +137,52 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nw = (gridDim.x * kBlock) >> 5;
-  double acc[2] = {0.0, 0.0};
-  for (int s = gw; s < a.K.nslices; s += nw) {
-    const int i = s * kSlice + lane;
-    const bool valid = i < a.m;
+  // per-thread partials in the iterate precision (a thread sums a few rows);
+  // FP64 only across threads: FP64 throughput on this GPU is ~1/60 of FP32
+  T acc_dy2 = 0, acc_int = 0;
+  int ob[U + 1];
+  slice_offsets<T, U>(a.K, gw * U, ob);
+  for (int s0 = gw * U; s0 < a.K.nslices; s0 += nw * U) {
+    int nb[U + 1];
+    slice_offsets<T, U>(a.K, s0 + nw * U, nb);  // next group, one iteration ahead
     // row operands do not depend on the product: load them first so their
     // latency overlaps the matrix stream
-    T ko = 0, yo = 0, qi = 0, lo = 0, yb = 0;
-    if (valid) {
-      ko = kxc[i];
-      yo = yc[i];
-      qi = a.q[i];
-      if (i >= a.m_eq) lo = dual_floor(a.ylo, i, a.m_eq);
-      if (pw != 0.0) yb = a.ybar[i];
+    T ko[U], yo[U], qi[U], lo[U], yb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = (s0 + u) * kSlice + lane;
+      ko[u] = yo[u] = qi[u] = lo[u] = yb[u] = 0;
+      if (i < a.m) {
+        ko[u] = kxc[i];
+        yo[u] = yc[i];
+        qi[u] = a.q[i];
+        if (i >= a.m_eq) lo[u] = dual_floor(a.ylo, i, a.m_eq);
+        if (has_pw) yb[u] = a.ybar[i];
+      }
     }
-    const T kx = sell_dot(a.K, s, lane, xn);
-    if (valid) {
-      T t = qi - (T)2 * kx;
-      t = t + ko;
-      T v = yo + sigma * t;
-      if (i >= a.m_eq) v = max(v, lo);
-      kxn[i] = kx;
-      yn[i] = v;
-      if (pw != 0.0) a.ybar[i] = yb + (T)pw * yo;
-      const double dy = (double)v - (double)yo;
-      const double dk = (double)kx - (double)ko;
-      acc[0] += dy * dy;
-      acc[1] += dy * dk;
+    T kx[U];
+    sell_dot_pre<T, U>(a.K, ob, lane, xn, kx);
+#pragma unroll
+    for (int u = 0; u <= U; ++u) ob[u] = nb[u];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = (s0 + u) * kSlice + lane;
+      if (i < a.m) {
+        T t = qi[u] - (T)2 * kx[u];
+        t = t + ko[u];
+        T v = yo[u] + sigma * t;
+        if (i >= a.m_eq) v = max(v, lo[u]);
+        kxn[i] = kx[u];
+        yn[i] = v;
+        if (has_pw) a.ybar[i] = yb[u] + pwT * yo[u];
+        const T dy = v - yo[u];
+        const T dk = kx[u] - ko[u];
+        acc_dy2 += dy * dy;
+        acc_int += dy * dk;
+      }
     }
   }
+  double acc[2] = {(double)acc_dy2, (double)acc_int};
   if (publish_partials<2>(acc, a.partials, &st->counter)) {
     double tot[2];
     final_sum<2>(a.partials, gridDim.x, tot);
@@ -140,13 +193,15 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kBlock, 6) k_adjoint(IterArgs<T> a) {
+template <class T, int U>
+__global__ void __launch_bounds__(kBlock) k_adjoint(IterArgs<T> a) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
   const int acc_last = st->accepted_last;
   const double wl = st->w_last;
+  const bool upd_avg = acc_last && wl != 0.0;
+  const T wlT = (T)wl;
   const T tau = (T)(st->eta / st->omega);
   const T* __restrict__ yc = a.y[p];
   const T* __restrict__ xc = a.x[p];
@@ -155,30 +210,46 @@ __global__ void __launch_bounds__(kBlock, 6) k_adjoint(IterArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nw = (gridDim.x * kBlock) >> 5;
-  double acc[1] = {0.0};
-  for (int s = gw; s < a.KT.nslices; s += nw) {
-    const int j = s * kSlice + lane;
-    const bool valid = j < a.n;
-    T x0 = 0, cj = 0, lj = 0, uj = 0, xb = 0, g = 0;
-    if (valid) {
-      x0 = xc[j];
-      cj = a.c[j];
-      lj = a.l[j];
-      uj = a.u[j];
-      if (acc_last && wl != 0.0) xb = a.xbar[j];
-      if (!acc_last) g = kty[j];
+  T acc_dx2 = 0;
+  int ob[U + 1];
+  if (acc_last) slice_offsets<T, U>(a.KT, gw * U, ob);
+  for (int s0 = gw * U; s0 < a.KT.nslices; s0 += nw * U) {
+    int nb[U + 1];
+    if (acc_last) slice_offsets<T, U>(a.KT, s0 + nw * U, nb);  // one iteration ahead
+    T x0[U], cj[U], lj[U], uj[U], xb[U], g[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = (s0 + u) * kSlice + lane;
+      x0[u] = cj[u] = lj[u] = uj[u] = xb[u] = g[u] = 0;
+      if (j < a.n) {
+        x0[u] = xc[j];
+        cj[u] = a.c[j];
+        lj[u] = a.l[j];
+        uj[u] = a.u[j];
+        if (upd_avg) xb[u] = a.xbar[j];
+        if (!acc_last) g[u] = kty[j];
+      }
     }
-    if (acc_last) g = sell_dot(a.KT, s, lane, yc);
-    if (valid) {
-      if (acc_last) kty[j] = g;
-      if (acc_last && wl != 0.0) a.xbar[j] = xb + (T)wl * x0;
-      T v = x0 - tau * (cj - g);
-      v = min(max(v, lj), uj);
-      xn[j] = v;
-      const double d = (double)v - (double)x0;
-      acc[0] += d * d;
+    if (acc_last) {
+      sell_dot_pre<T, U>(a.KT, ob, lane, yc, g);
+#pragma unroll
+      for (int u = 0; u <= U; ++u) ob[u] = nb[u];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = (s0 + u) * kSlice + lane;
+      if (j < a.n) {
+        if (acc_last) kty[j] = g[u];
+        if (upd_avg) a.xbar[j] = xb[u] + wlT * x0[u];
+        T v = x0[u] - tau * (cj[u] - g[u]);
+        v = min(max(v, lj[u]), uj[u]);
+        xn[j] = v;
+        const T d = v - x0[u];
+        acc_dx2 += d * d;
+      }
     }
   }
+  double acc[1] = {(double)acc_dx2};
   if (publish_partials<1>(acc, a.partials, &st->counter)) {
     double tot[1];
     final_sum<1>(a.partials, gridDim.x, tot);
@@ -314,13 +385,21 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
 }
 
 template <class T>
-void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s) {
-  k_dual<T><<<grid, kBlock, 0, s>>>(a);
+void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
+  switch (unroll) {
+    case 2: k_dual<T, 2><<<grid, kBlock, 0, s>>>(a); break;
+    case 4: k_dual<T, 4><<<grid, kBlock, 0, s>>>(a); break;
+    default: k_dual<T, 1><<<grid, kBlock, 0, s>>>(a); break;
+  }
 }
 
 template <class T>
-void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s) {
-  k_adjoint<T><<<grid, kBlock, 0, s>>>(a);
+void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
+  switch (unroll) {
+    case 2: k_adjoint<T, 2><<<grid, kBlock, 0, s>>>(a); break;
+    case 4: k_adjoint<T, 4><<<grid, kBlock, 0, s>>>(a); break;
+    default: k_adjoint<T, 1><<<grid, kBlock, 0, s>>>(a); break;
+  }
 }
 
 void launch_state_init(DevState* st, const RoundInit& r, const double* scalars, cudaStream_t s) {
@@ -329,8 +408,8 @@ void launch_state_init(DevState* st, const RoundInit& r, const double* scalars, 
 
 int blocks_per_sm_iter() {
   int best = 1 << 30;
-  const void* fns[4] = {(const void*)&k_dual<double>, (const void*)&k_adjoint<double>,
-                        (const void*)&k_dual<float>, (const void*)&k_adjoint<float>};
+  const void* fns[4] = {(const void*)&k_dual<double, 1>, (const void*)&k_adjoint<double, 1>,
+                        (const void*)&k_dual<float, 1>, (const void*)&k_adjoint<float, 1>};
   for (const void* f : fns) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0) != cudaSuccess) b = 4;
@@ -341,9 +420,9 @@ int blocks_per_sm_iter() {
 
 template void launch_init_iterates<double>(const IterArgs<double>&, int, cudaStream_t);
 template void launch_init_iterates<float>(const IterArgs<float>&, int, cudaStream_t);
-template void launch_dual<double>(const IterArgs<double>&, int, cudaStream_t);
-template void launch_dual<float>(const IterArgs<float>&, int, cudaStream_t);
-template void launch_adjoint<double>(const IterArgs<double>&, int, cudaStream_t);
-template void launch_adjoint<float>(const IterArgs<float>&, int, cudaStream_t);
+template void launch_dual<double>(const IterArgs<double>&, int, cudaStream_t, int);
+template void launch_dual<float>(const IterArgs<float>&, int, cudaStream_t, int);
+template void launch_adjoint<double>(const IterArgs<double>&, int, cudaStream_t, int);
+template void launch_adjoint<float>(const IterArgs<float>&, int, cudaStream_t, int);
 
 }  // namespace ucpdhg

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a) {
   const int p = st->par;
   const double wsum = st->wsum, pw = st->pending_w, inv_dp = st->inv_dp;
   const bool has_avg = wsum > 0.0;
+  const double iw = has_avg ? 1.0 / wsum : 0.0;
   const T* __restrict__ xc = a.x[p];
   const T* __restrict__ xb = a.xbar;
   const T* __restrict__ yc = a.y[p];
@@ -55,10 +56,10 @@ __global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a) {
         yb = yb + (T)pw * yo;
         a.ybar[i] = yb;
       }
-      const double kx_avg = has_avg ? d1 / wsum : d0;
+      const double kx_avg = has_avg ? d1 * iw : d0;
       if (has_avg) a.Kz_avg[i] = kx_avg;
-      const double y_avg = has_avg ? (double)yb / wsum : (double)yo;
-      const double qr = a.q_res[i], qo = a.q_obj[i], dr = a.Dr[i];
+      const double y_avg = has_avg ? (double)yb * iw : (double)yo;
+      const double qr = a.q_res[i], qo = a.q_obj[i], sr = inv_dp * a.iDr[i];
       const double yanc = (double)a.ya[i];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a) {
         const double yv = c ? y_avg : (double)yo;
         double r = qr - kx;
         if (i >= a.m_eq) r = fmax(r, 0.0);
-        const double ru = r * inv_dp / dr;
+        const double ru = r * sr;
         const double dd = yv - yanc;
         acc[c * kRowSums + 0] += r * r;
         acc[c * kRowSums + 1] += ru * ru;
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a) {
   const int p = st->par;
   const double wsum = st->wsum, inv_dd = st->inv_dd;
   const bool has_avg = wsum > 0.0;
+  const double iw = has_avg ? 1.0 / wsum : 0.0;
   const T* __restrict__ yc = a.y[p];
   const T* __restrict__ yb = a.ybar;
   const T* __restrict__ xc = a.x[p];
@@ -113,12 +115,12 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a) {
     }
     const int j = s * kSlice + lane;
     if (j < a.n) {
-      const double kty_avg = has_avg ? e1 / wsum : e0;
+      const double kty_avg = has_avg ? e1 * iw : e0;
       if (has_avg) a.KTz_avg[j] = kty_avg;
-      const double x_avg = has_avg ? (double)a.xbar[j] / wsum : (double)xc[j];
+      const double x_avg = has_avg ? (double)a.xbar[j] * iw : (double)xc[j];
       const double lo = a.l_obj[j], up = a.u_obj[j];
       const bool lf = isfinite(lo), uf = isfinite(up);
-      const double cr = a.c_res[j], co = a.c_obj[j], dc = a.Dc[j];
+      const double cr = a.c_res[j], co = a.c_obj[j], sc = inv_dd * a.iDc[j];
       const double xanc = (double)a.xa[j];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a) {
         const double lam = cr - kty;
         const double proj = (lf ? fmax(lam, 0.0) : 0.0) + (uf ? fmin(lam, 0.0) : 0.0);
         const double rd = lam - proj;
-        const double rdu = rd * inv_dd / dc;
+        const double rdu = rd * sc;
         const double lp = proj * inv_dd;
         const double bnd = (lf ? lo * fmax(lp, 0.0) : 0.0) - (uf ? up * fmax(-lp, 0.0) : 0.0);
         const double dx = xv - xanc;
@@ -234,7 +236,12 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
       st->k_tol[i] = st->k_offset + st->k;
     }
   int done = 0, status = 0;
-  if (isnan(rel[0]) || isnan(rel[1]) || isinf(rel[0])) {
+  // fmax/fmin (and the bound clamps of the iterations) drop NaNs, so test the
+  // raw sums: any NaN/Inf in the data or the iterates shows up in one of them
+  bool finite = true;
+  for (int k = 0; k < 2 * kRowSums; ++k) finite = finite && isfinite(rs[k]);
+  for (int k = 0; k < 2 * kColSums; ++k) finite = finite && isfinite(cs[k]);
+  if (!finite || !isfinite(rel[0]) || !isfinite(rel[1])) {
     done = 1;
     status = PDHG_STATUS_NUMERIC;
     st->numeric = 1;

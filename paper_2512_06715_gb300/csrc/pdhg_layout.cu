@@ -206,7 +206,7 @@ __global__ void k_scale_vals(SellView<double> A, double* val, const double* __re
 // max |K~| as per-block partials (deterministic final pass in k_prepare_final).
 __global__ void k_scale_vecs(double* c_s, double* l_s, double* u_s, double* q_s,
                              const double* __restrict__ Dr, const double* __restrict__ Dc, int64_t n,
-                             int64_t m, double* partials) {
+                             int64_t m, double* partials, double* iDr, double* iDc) {
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   int64_t N = n > m ? n : m;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
@@ -217,12 +217,14 @@ __global__ void k_scale_vecs(double* c_s, double* l_s, double* u_s, double* q_s,
       double cs = d * c;
       c_s[t] = cs;
       v[2] += cs * cs;
+      iDc[t] = 1.0 / d;
       l_s[t] = l_s[t] / d;
       u_s[t] = u_s[t] / d;
     }
     if (t < m) {
       double q = q_s[t];
       v[1] += q * q;
+      iDr[t] = 1.0 / Dr[t];
       double qs = Dr[t] * q;
       q_s[t] = qs;
       v[3] += qs * qs;
@@ -373,7 +375,7 @@ void launch_prepare(Workspace* w, cudaStream_t s) {
   double* part_vec = w->partials;
   double* part_max = w->partials + (size_t)kMaxBlocks * 16;
   k_scale_vecs<<<gv, kBlock, 0, s>>>(w->c_s, w->l_s, w->u_s, w->q_s, w->Dr, w->Dc, w->n, w->m,
-                                     part_vec);
+                                     part_vec, w->iDr, w->iDc);
   const int gm = vec_grid(w->K.nnz_pad, sms);
   k_absmax_partial<<<gm, kBlock, 0, s>>>(w->K.val64, w->K.nnz_pad, part_max);
   k_prepare_final<<<1, kBlock, 0, s>>>(part_vec, gv, part_max, gm, w->scalars);

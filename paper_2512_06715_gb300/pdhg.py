@@ -35,7 +35,7 @@ class pdhg_opts(C.Structure):
                 ("ir_max_rounds", C.c_int32), ("trace", C.c_int32),
                 ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
                 ("bound_obj_rescale", C.c_int32), ("artificial_total", C.c_int32),
-                ("host_loop", C.c_int32), ("cancel_flag", C.c_void_p)]
+                ("host_loop", C.c_int32), ("autotune", C.c_int32), ("cancel_flag", C.c_void_p)]
 
 
 class pdhg_result(C.Structure):
@@ -72,6 +72,7 @@ _SIGS = {
     "pdhg_apply_K": ([C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "pdhg_get_trace": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(C.c_int64),
                         C.POINTER(C.c_int64)], C.c_int),
+    "pdhg_get_tuning": ([C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
     "pdhg_time_kernels": ([C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p], C.c_int),
 }
@@ -213,6 +214,12 @@ class Workspace:
         _check(lib().pdhg_get_trace(self.ws, a.ctypes.data, cap_a, c.ctypes.data, cap_c, C.byref(na),
                                     C.byref(nc)), "pdhg_get_trace")
         return a[: min(na.value, cap_a)], c[: min(nc.value, cap_c)]
+
+    def tuning(self):
+        cfg = (C.c_int32 * 8)()
+        _check(lib().pdhg_get_tuning(self.ws, cfg), "pdhg_get_tuning")
+        names = ("unroll_dual", "grid_dual", "unroll_adj", "grid_adj")
+        return {"fp64": dict(zip(names, cfg[0:4])), "fp32": dict(zip(names, cfg[4:8]))}
 
     def time_kernels(self, precision=PREC_FP64, reps=20, stream=None):
         md, ma, bd, ba = C.c_double(), C.c_double(), C.c_double(), C.c_double()
