@@ -173,6 +173,30 @@ int pdhg_backward(void *ws, double g_cost, const double *g_x, double *grad_q, do
 /* Message of the last failure on this thread ("" if none). */
 const char *pdhg_last_error(void);
 
+/* Ruiz + Pock-Chambolle rescaling factors WITHOUT any device allocation.
+ * The paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc (a caching allocator of another framework owns the device
+ * memory, a fixed memory budget is set up front, or an allocation's implicit
+ * synchronisation is not allowed).  Computes the same Dr [m], Dc [n] as
+ * pdhg_prepare + pdhg_get_scaling (ruiz_iters l_inf passes, then one alpha = 1
+ * Pock-Chambolle pass if pock_chambolle != 0), straight from the CSR of `prob`
+ * (row_ptr, col, val, n, m; the other fields are ignored).  Dr, Dc: device,
+ * caller-owned, written in original order.
+ *   - Scratch: one file-scope device array of 2^21 doubles (16 MiB) that every
+ *     GPU loading the library holds until the process exits.  n > 2^21 is
+ *     rejected with PDHG_ERR_UNSUPPORTED before any device work.
+ *   - No cudaMalloc, cudaFree or allocating library call is made.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and finds the previous call's contents in
+ *     it (it clears what must start at zero); calls that overlap on the GPU,
+ *     in different streams or threads, race on it.
+ *   - Column statistics use FP64 atomics for the Pock-Chambolle sums, so the
+ *     last bits may differ from the workspace path and between calls. */
+int pdhg_rescale_noalloc(const pdhg_problem *prob, int32_t ruiz_iters, int32_t pock_chambolle,
+                         double *Dr, double *Dc, void *stream);
+
 /* ---- diagnostics (kernel-level tests and measurement) -------------------- */
 
 /* Load the values and run the rescaling of a solve without iterating. */

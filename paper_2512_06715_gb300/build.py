@@ -31,6 +31,7 @@ CUDA_SOURCES = [
     "pdhg_kkt.cu",
     "pdhg_batched.cu",
     "pdhg_adjoint.cu",
+    "pdhg_noalloc.cu",
 ]
 
 

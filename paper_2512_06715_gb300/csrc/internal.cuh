@@ -112,6 +112,9 @@ struct Workspace {
   void* adjoint = nullptr;
 };
 
+// message of the last failure on this thread (pdhg_last_error), pdhg_api.cu
+extern thread_local std::string g_err;
+
 // pdhg_layout.cu
 void launch_prepare(Workspace* w, cudaStream_t s);
 void launch_spmv64(const SellView<double>& A, const double* x, double* y, int grid, cudaStream_t s);

@@ -73,6 +73,8 @@ _SIGS = {
     "pdhg_get_trace": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(C.c_int64),
                         C.POINTER(C.c_int64)], C.c_int),
     "pdhg_get_tuning": ([C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
+    "pdhg_rescale_noalloc": ([C.POINTER(pdhg_problem), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                              C.c_void_p], C.c_int),
     "pdhg_time_kernels": ([C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p], C.c_int),
 }
