@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--host-loop", action="store_true",
                    help="launch the per-check bodies from the host instead of one CUDA graph "
                         "(same kernels; profilers cannot see kernels inside conditional graphs)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="default launch shapes instead of timing the variants (profiler replays "
+                        "distort those timings)")
     return p.parse_args()
 
 
@@ -195,7 +198,7 @@ def run_ours(args):
 
     def opts(prec, attempts, tol=1e-8, tl=600.0):
         return pdhg.default_opts(precision=prec, max_iters=attempts, tol=tol, time_limit_s=tl,
-                                 host_loop=int(args.host_loop))
+                                 host_loop=int(args.host_loop), autotune=int(not args.no_autotune))
 
     ws = pdhg.Workspace.from_instance(inst, opts("mixed", args.attempts), device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
