@@ -94,7 +94,7 @@ typedef struct pdhg_opts {
   int32_t pock_chambolle;   /* 1: one Pock-Chambolle alpha=1 pass (1)                 */
   double ir_first_tol;      /* mixed: rel_kkt target of the first FP32 round (1e-4)   */
   double ir_reduction;      /* mixed: per-round reduction of rel_kkt (0.1)            */
-  int32_t ir_max_rounds;    /* mixed: refinement rounds after the first (100)         */
+  int32_t ir_max_rounds;    /* mixed: refinement rounds after the first (1000)        */
   int32_t trace;            /* 1: record per-attempt/per-check trace (testing) (0)    */
   double fixed_eta;         /* > 0: constant steps eta/omega, no restarts (0)         */
   double fixed_omega;       /* primal weight in fixed-step mode                       */

@@ -147,4 +147,9 @@ void launch_output(Workspace* w, double* x_out, double* y_out, cudaStream_t s);
 template <class T>
 IterArgs<T> make_args(Workspace* w);
 
+// pdhg_batched.cu: frees the batched buffers and graph of a workspace
+void release_batched(Workspace* w);
+// pdhg_adjoint.cu: frees the adjoint's scratch
+void release_adjoint(Workspace* w);
+
 }  // namespace ucpdhg

@@ -295,6 +295,8 @@ static int ensure_trace(Workspace* w) {
 }
 
 static void release(Workspace* w) {
+  release_batched(w);
+  release_adjoint(w);
   for (int i = 0; i < 2; ++i) {
     if (w->graph_exec[i]) cudaGraphExecDestroy(w->graph_exec[i]);
     if (w->graph[i]) cudaGraphDestroy(w->graph[i]);
@@ -490,7 +492,7 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->pock_chambolle = 1;
   o->ir_first_tol = 1e-4;
   o->ir_reduction = 0.1;
-  o->ir_max_rounds = 100;
+  o->ir_max_rounds = 1000;
   o->trace = 0;
   o->fixed_eta = 0.0;
   o->fixed_omega = 0.0;
@@ -657,6 +659,7 @@ extern "C" int pdhg_set_opts(void* ws, const pdhg_opts* opts) {
   Workspace* w = (Workspace*)ws;
   w->opts = *opts;
   drop_graphs(w);  // graphs bake the cancel and trace pointers in
+  release_batched(w);
   return ensure_trace(w);
 }
 

@@ -155,6 +155,34 @@ def build_instance(n_bus: int, n_line: int, n_gen: int, n_periods: int, seed: in
     return inst
 
 
+def node_fixings(inst: UCInstance, n_nodes: int, seed0: int = 1000, lo_frac: float = 0.01,
+                 hi_frac: float = 0.05):
+    """Bounds of branch-and-bound node LPs: node k fixes a random U(lo_frac, hi_frac)
+    share of the commitment variables u_gt to 0 or 1 (p = 1/2) through l = u, with
+    numpy's PCG64 seeded by seed0 + k.  Fixings of one generator to opposite values
+    stay at least max(min up, min down) + 1 periods apart, so that with shed/spill
+    slacks every node stays feasible.  Returns (l_b, u_b), each [n_nodes, n]."""
+    T, G = inst.idx_u.shape
+    l_b = np.repeat(inst.l[None, :], n_nodes, axis=0)
+    u_b = np.repeat(inst.u[None, :], n_nodes, axis=0)
+    sep = np.maximum(inst.gen_min_up, inst.gen_min_dn) + 1
+    for k in range(n_nodes):
+        rng = np.random.default_rng(seed0 + k)
+        frac = rng.uniform(lo_frac, hi_frac)
+        count = max(1, int(round(frac * T * G)))
+        cells = rng.permutation(T * G)[:count]
+        vals = rng.integers(0, 2, size=count)
+        fixed = {}  # g -> list of (t, v)
+        for cell, v in zip(cells, vals):
+            t, g = divmod(int(cell), G)
+            if any(v2 != v and abs(t - t2) < sep[g] for t2, v2 in fixed.get(g, [])):
+                continue
+            fixed.setdefault(g, []).append((t, int(v)))
+            j = inst.idx_u[t, g]
+            l_b[k, j] = u_b[k, j] = float(v)
+    return l_b, u_b
+
+
 # Workloads named by what they are (bus count, generators, horizon).
 WORKLOADS = {
     # 24 buses in a ring + 14 chords, 33 generators, 24 hourly periods

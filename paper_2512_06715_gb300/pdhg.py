@@ -190,6 +190,21 @@ class Workspace:
                "pdhg_solve")
         return x, y, r.to_dict()
 
+    def solve_batched(self, l_b, u_b, stream=None, want_y=True):
+        """B node LPs sharing K, c, q with bounds l_b, u_b [B, n] (original order).
+        Returns (x [B, n], y [B, m] or None, list of result dicts)."""
+        import torch
+        l_b = torch.as_tensor(l_b, dtype=torch.float64, device=self.device).contiguous()
+        u_b = torch.as_tensor(u_b, dtype=torch.float64, device=self.device).contiguous()
+        B = int(l_b.shape[0])
+        x = torch.empty((B, self.n), dtype=torch.float64, device=self.device)
+        y = torch.empty((B, self.m), dtype=torch.float64, device=self.device) if want_y else None
+        res = (pdhg_result * B)()
+        _check(lib().pdhg_solve_batched(self.ws, B, l_b.data_ptr(), u_b.data_ptr(), x.data_ptr(),
+                                        y.data_ptr() if y is not None else None, res, _stream_ptr(stream)),
+               "pdhg_solve_batched")
+        return x, y, [r.to_dict() for r in res]
+
     def prepare(self, stream=None):
         _check(lib().pdhg_prepare(self.ws, _stream_ptr(stream)), "pdhg_prepare")
 

@@ -1,0 +1,65 @@
+"""Batched node LPs (pdhg_solve_batched) against single-instance solves and the oracle."""
+import numpy as np
+import pytest
+
+from oracle.lp import kkt, lp_from_arrays, max_violation
+from paper_2512_06715_gb300.instances import build_instance, node_fixings
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_06715_gb300 import build
+    build.build()
+
+
+def _node_lp(inst, l, u):
+    return lp_from_arrays(inst.row_ptr, inst.col, inst.val, inst.q, inst.c, l, u, inst.m_eq)
+
+
+@pytest.mark.parametrize("B,tol", [(1, 1e-8), (8, 1e-8), (33, 1e-6)])
+def test_batched_matches_single_solves(B, tol):
+    """Each node of the batch agrees with the same node solved alone (objective
+    within 100 tol relative) and the oracle recomputes its rel-KKT <= 2 tol.
+    B = 33 runs the 64-slot layout with 31 idle slots."""
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst = build_instance(12, 18, 10, 12, seed=3, with_slack=True)
+    l_b, u_b = node_fixings(inst, B)
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=tol, time_limit_s=120.0))
+    xb, yb, rb = ws.solve_batched(l_b, u_b)
+    xb, yb = xb.cpu().numpy(), yb.cpu().numpy()
+    check = range(B) if B <= 8 else [0, 1, B // 2, B - 1]
+    for k in check:
+        assert rb[k]["status_name"] == "optimal", (k, rb[k])
+        lp = _node_lp(inst, l_b[k], u_b[k])
+        c = kkt(lp, xb[k], yb[k])
+        assert c.rel_kkt <= 2 * tol, (k, c.rel_kkt, rb[k]["rel_kkt"])
+        assert max_violation(lp, xb[k]) <= 100 * tol * max(1.0, np.abs(lp.q).max())
+        # the same node solved alone
+        single = Workspace(inst.row_ptr, inst.col, inst.val, inst.c, l_b[k], u_b[k], inst.q, inst.m_eq,
+                           default_opts(precision="mixed", tol=tol, time_limit_s=120.0))
+        xs, ys, rs = single.solve()
+        assert rs["status_name"] == "optimal"
+        ps = kkt(lp, xs.cpu().numpy(), ys.cpu().numpy()).primal_obj
+        assert abs(c.primal_obj - ps) <= 100 * tol * abs(ps), (k, c.primal_obj, ps)
+        single.close()
+    ws.close()
+
+
+def test_batched_nodes_bound_the_root():
+    """Fixing commitments only tightens the relaxation: every node's optimum is
+    at least the root LP optimum."""
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst = build_instance(12, 18, 10, 12, seed=4, with_slack=True)
+    l_b, u_b = node_fixings(inst, 16, seed0=2000)
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=1e-8, time_limit_s=120.0))
+    _, _, root = ws.solve()
+    xb, yb, rb = ws.solve_batched(l_b, u_b)
+    assert all(r["status_name"] == "optimal" for r in rb)
+    for r in rb:
+        assert r["primal_obj"] >= root["primal_obj"] * (1 - 1e-7)
+    ws.close()
