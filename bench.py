@@ -64,7 +64,7 @@ def parse():
 def algorithmic_bytes(n, m, nnz, elt):
     """Per attempt, CSR-equivalent: matrix stream (value + int32 column + int32 row
     pointer) of K and K^T, each gathered vector once, each streamed vector once."""
-    dual = nnz * (elt + 4) + 4 * m + elt * n + elt * m * (8 if elt == 4 else 7)
+    dual = nnz * (elt + 4) + 4 * m + 2 * elt * n + elt * m * (6 if elt == 4 else 5)
     adj = nnz * (elt + 4) + 4 * n + elt * m + elt * n * 8
     return dual, adj
 

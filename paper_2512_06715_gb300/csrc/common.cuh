@@ -89,7 +89,6 @@ struct IterArgs {
   SellView<T> K, KT;
   T* x[2];
   T* y[2];
-  T* Kx[2];
   T* KTy[2];
   T* xbar;  // weighted sums (not divided)
   T* ybar;
@@ -186,6 +185,13 @@ __device__ __forceinline__ void final_sum(const double* partials, int nblocks, d
   block_sum<NV>(v, smem);
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = v[k];
+}
+
+// (k+1)^(-e) of the step-size rule in FP32 (relative error ~1e-6): an FP64
+// pow on the serial tail of every attempt would cost microseconds on a GPU
+// whose FP64 rate is ~1/60 of FP32, and the rule is a heuristic factor.
+__device__ __forceinline__ double step_power(int64_t k1, double e) {
+  return (double)exp2f(-(float)e * log2f((float)k1));
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -27,7 +27,6 @@ template <class T>
 struct IterBufs {
   T* x[2] = {nullptr, nullptr};
   T* y[2] = {nullptr, nullptr};
-  T* Kx[2] = {nullptr, nullptr};
   T* KTy[2] = {nullptr, nullptr};
   T* xbar = nullptr;
   T* ybar = nullptr;

@@ -72,7 +72,6 @@ IterArgs<T> make_args(Workspace* w) {
   for (int i = 0; i < 2; ++i) {
     a.x[i] = b->x[i];
     a.y[i] = b->y[i];
-    a.Kx[i] = b->Kx[i];
     a.KTy[i] = b->KTy[i];
   }
   a.xbar = b->xbar;
@@ -117,7 +116,6 @@ static int alloc_bufs(Workspace* w, IterBufs<T>* b) {
   for (int i = 0; i < 2; ++i) {
     DALLOC(b->x[i], w->n);
     DALLOC(b->y[i], w->m);
-    DALLOC(b->Kx[i], w->m);
     DALLOC(b->KTy[i], w->n);
   }
   DALLOC(b->xbar, w->n);
@@ -814,11 +812,11 @@ extern "C" int pdhg_time_kernels(void* ws, int32_t precision, int32_t reps, doub
   const double n = (double)w->n, m = (double)w->m, nnz = (double)w->nnz;
   // algorithmic bytes: CSR-equivalent matrix stream (value + int32 column +
   // int32 row pointer), each gathered vector once, each streamed vector once.
-  // dual: y, Kx, q, ybar read; ybar, Kx', y' written (+ y_lo read in FP32 mode)
-  // adjoint: x, xbar, c, l, u read; xbar, K^T y', x'' written
+  // dual: x' and x gathered; y, q, ybar read; ybar, y' written (+ y_lo in FP32 mode)
+  // adjoint: y' gathered; x, xbar, c, l, u read; xbar, K^T y', x'' written
   if (ms_dual) *ms_dual = t_d / reps;
   if (ms_adj) *ms_adj = t_a / reps;
-  if (bytes_dual) *bytes_dual = nnz * (sz + 4.0) + 4.0 * m + sz * n + sz * m * (f32 ? 8.0 : 7.0);
+  if (bytes_dual) *bytes_dual = nnz * (sz + 4.0) + 4.0 * m + 2.0 * sz * n + sz * m * (f32 ? 6.0 : 5.0);
   if (bytes_adj) *bytes_adj = nnz * (sz + 4.0) + 4.0 * n + sz * m + sz * n * 8.0;
   return PDHG_OK;
 }

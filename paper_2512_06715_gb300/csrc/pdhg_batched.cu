@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
         const int64_t k = I.k + 1;
         I.k = k;
         I.k_total += 1;
-        const double eta_next = fmin((1.0 - pow((double)(k + 1), -g->red_exp)) * eta_max,
-                                     (1.0 + pow((double)(k + 1), -g->grow_exp)) * eta);
+        const double eta_next = fmin((1.0 - step_power(k + 1, g->red_exp)) * eta_max,
+                                     (1.0 + step_power(k + 1, g->grow_exp)) * eta);
         const int accept = eta <= eta_max;
         if (accept) {
           I.par = 1 - I.par;

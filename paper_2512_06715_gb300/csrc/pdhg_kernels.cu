@@ -1,7 +1,8 @@
 // The two kernels of one PDHG step attempt (Sec. II.E iteration, PDLP form):
 //
-//   k_dual    : K x' (sliced ELL SpMV, warp per 32-row slice) fused with the
-//               projected dual step y' = max(y_lo, y + sigma (q - 2 K x' + K x)),
+//   k_dual    : K x' and K x (sliced ELL, warp per 32-row slice, one matrix
+//               pass gathering both) fused with the projected dual step
+//               y' = max(y_lo, y + sigma (q - 2 K x' + K x)),
 //               the lazy y-average update, and the FP64 partial sums ||dy||^2 and
 //               dy^T K dx.  The block that finishes last reduces the partials in
 //               fixed order and takes the adaptive step decision (accept/reject,
@@ -61,6 +62,44 @@ __device__ __forceinline__ void sell_dot_pre(const SellView<T>& A, const int (&o
   }
 }
 
+// Two row products at once, K x1 and K x2, sharing the matrix stream (the
+// second gather hits L2: the iterate vectors are a few MB).
+template <class T, int U>
+__device__ __forceinline__ void sell_dot2_pre(const SellView<T>& A, const int (&ob)[U + 1], int lane,
+                                              const T* __restrict__ x1, const T* __restrict__ x2,
+                                              T (&acc1)[U], T (&acc2)[U]) {
+  int o0[U], w[U];
+  int wmax = 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    o0[u] = ob[u] + lane;
+    w[u] = (ob[u + 1] - ob[u]) >> 5;
+    wmax = max(wmax, w[u]);
+    acc1[u] = 0;
+    acc2[u] = 0;
+  }
+  for (int k0 = 0; k0 < wmax; k0 += 4) {
+    int c[U][4];
+    T v[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool ok = k0 + e < w[u];
+        c[u][e] = ok ? __ldg(A.col + o0[u] + (k0 + e) * kSlice) : 0;
+        v[u][e] = ok ? __ldg(A.val + o0[u] + (k0 + e) * kSlice) : (T)0;
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (k0 + e < w[u]) {
+          acc1[u] += v[u][e] * __ldg(x1 + c[u][e]);
+          acc2[u] += v[u][e] * __ldg(x2 + c[u][e]);
+        }
+  }
+}
+
 template <class T, int U>
 __device__ __forceinline__ void sell_dot_multi(const SellView<T>& A, int s0, int lane,
                                                const T* __restrict__ x, T (&acc)[U]) {
@@ -85,8 +124,8 @@ __device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, doub
   const double eta_max = interaction > 0.0 ? movement / interaction : INFINITY;
   const int64_t k = st->k + 1;
   st->k = k;
-  double eta_next = fmin((1.0 - pow((double)(k + 1), -st->red_exp)) * eta_max,
-                         (1.0 + pow((double)(k + 1), -st->grow_exp)) * eta);
+  double eta_next = fmin((1.0 - step_power(k + 1, st->red_exp)) * eta_max,
+                         (1.0 + step_power(k + 1, st->grow_exp)) * eta);
   int accept = eta <= eta_max;
   if (st->fixed) {
     accept = 1;
@@ -130,10 +169,9 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
   const T pwT = (T)pw;
   const T sigma = (T)(st->eta * st->omega);
   const T* __restrict__ xn = a.x[1 - p];
+  const T* __restrict__ xc = a.x[p];
   const T* __restrict__ yc = a.y[p];
-  const T* __restrict__ kxc = a.Kx[p];
   T* __restrict__ yn = a.y[1 - p];
-  T* __restrict__ kxn = a.Kx[1 - p];
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nw = (gridDim.x * kBlock) >> 5;
@@ -147,21 +185,22 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
     slice_offsets<T, U>(a.K, s0 + nw * U, nb);  // next group, one iteration ahead
     // row operands do not depend on the product: load them first so their
     // latency overlaps the matrix stream
-    T ko[U], yo[U], qi[U], lo[U], yb[U];
+    T yo[U], qi[U], lo[U], yb[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = (s0 + u) * kSlice + lane;
-      ko[u] = yo[u] = qi[u] = lo[u] = yb[u] = 0;
+      yo[u] = qi[u] = lo[u] = yb[u] = 0;
       if (i < a.m) {
-        ko[u] = kxc[i];
         yo[u] = yc[i];
         qi[u] = a.q[i];
         if (i >= a.m_eq) lo[u] = dual_floor(a.ylo, i, a.m_eq);
         if (has_pw) yb[u] = a.ybar[i];
       }
     }
-    T kx[U];
-    sell_dot_pre<T, U>(a.K, ob, lane, xn, kx);
+    // K x' and K x in one pass: K x is recomputed instead of stored, which
+    // trades an L2 gather for a stream read and write of m values
+    T kx[U], ko[U];
+    sell_dot2_pre<T, U>(a.K, ob, lane, xn, xc, kx, ko);
 #pragma unroll
     for (int u = 0; u <= U; ++u) ob[u] = nb[u];
 #pragma unroll
@@ -172,7 +211,6 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
         t = t + ko[u];
         T v = yo[u] + sigma * t;
         if (i >= a.m_eq) v = max(v, lo[u]);
-        kxn[i] = kx[u];
         yn[i] = v;
         if (has_pw) a.ybar[i] = yb[u] + pwT * yo[u];
         const T dy = v - yo[u];
@@ -376,11 +414,8 @@ template <class T>
 void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
   (void)grid;
   k_init_vectors<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a);
-  int gk = (a.K.nslices + kWarps - 1) / kWarps;
   int gt = (a.KT.nslices + kWarps - 1) / kWarps;
-  if (gk > kMaxBlocks) gk = kMaxBlocks;
   if (gt > kMaxBlocks) gt = kMaxBlocks;
-  k_spmv_into<T><<<gk < 1 ? 1 : gk, kBlock, 0, s>>>(a.K, a.x[0], a.Kx[0]);
   k_spmv_into<T><<<gt < 1 ? 1 : gt, kBlock, 0, s>>>(a.KT, a.y[0], a.KTy[0]);
 }
 

@@ -342,10 +342,7 @@ __global__ void __launch_bounds__(kBlock) k_restart_apply(IterArgs<T> a) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
     if (t < a.m) {
-      if (to_avg) {
-        y[t] = (T)((double)a.ybar[t] / div);
-        a.Kx[p][t] = (T)a.Kz_avg[t];
-      }
+      if (to_avg) y[t] = (T)((double)a.ybar[t] / div);
       a.ya[t] = y[t];
       a.ybar[t] = 0;
     }

@@ -75,6 +75,30 @@ def test_invalid_params():
         build_instance(5, 3, 1, 1)  # fewer lines than the ring needs
 
 
+def test_node_fixings_rules():
+    """Node bounds fix 1-5% of the commitments to 0/1, only commitments, and keep
+    opposite fixings of a unit at least max(min up, min down) + 1 periods apart."""
+    from paper_2512_06715_gb300.instances import VAR_U, node_fixings
+    inst = build_instance(12, 18, 10, 24, seed=2, with_slack=True)
+    l_b, u_b = node_fixings(inst, 16, seed0=1000)
+    T, G = inst.idx_u.shape
+    sep = np.maximum(inst.gen_min_up, inst.gen_min_dn) + 1
+    for k in range(16):
+        changed = np.where((l_b[k] != inst.l) | (u_b[k] != inst.u))[0]
+        assert np.all(inst.var_kind[changed] == VAR_U)
+        assert 0 < changed.size <= int(round(0.05 * T * G)) + 1
+        assert np.all(l_b[k][changed] == u_b[k][changed])
+        for g in range(G):
+            fixed = [(t, l_b[k][inst.idx_u[t, g]]) for t in range(T)
+                     if l_b[k][inst.idx_u[t, g]] == u_b[k][inst.idx_u[t, g]]]
+            for t1, v1 in fixed:
+                for t2, v2 in fixed:
+                    if v1 != v2:
+                        assert abs(t1 - t2) >= sep[g]
+    l2, u2 = node_fixings(inst, 16, seed0=1000)
+    assert np.array_equal(l_b, l2) and np.array_equal(u_b, u2)
+
+
 def test_deterministic():
     a = workload("uc24_g33_T24", seed=3)
     b = workload("uc24_g33_T24", seed=3)
