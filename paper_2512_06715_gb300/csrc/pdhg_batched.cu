@@ -32,6 +32,8 @@ constexpr int kBThreads = kBWarps * 32;
 constexpr int kKktWarps = 4;          // smaller blocks for the FP64 check sweeps
 constexpr int kApplyRows = 4;         // rows per block of the elementwise kernels (x BP threads)
 constexpr int kRowS = 4, kColS = 5;   // per-candidate sums (as in the single-instance check)
+constexpr int kRowsPerWarp = 4;       // rows (columns) a warp sweeps together in kb_dual (kb_adjoint)
+static_assert(kRowsPerWarp == 4 && kSlice % kRowsPerWarp == 0, "int4/float4 entry loads");
 
 // Per-instance state (array of B structs in device memory).
 struct BInst {
@@ -181,39 +183,80 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
   float a_dy2[H], a_int[H];
 #pragma unroll
   for (int h = 0; h < H; ++h) a_dy2[h] = a_int[h] = 0.f;
-  for (int i = gw; i < a.m; i += nw) {
-    const int s = i >> 5, r = i & 31;
-    const int o0 = __ldg(a.K.off + s) + r;
-    const int w = (__ldg(a.K.off + s + 1) - __ldg(a.K.off + s)) >> 5;
-    float acc[H];
+  // gather base of each lane's instances (null: instance idle)
+  const float* xg[H];
 #pragma unroll
-    for (int h = 0; h < H; ++h) acc[h] = 0.f;
+  for (int h = 0; h < H; ++h) {
+    const int b = lane + 32 * h;
+    xg[h] = s_act[b] ? a.x[1 - s_par[b]] + b : nullptr;
+  }
+  const int nq = (a.m + kRowsPerWarp - 1) / kRowsPerWarp;
+  for (int qd = gw; qd < nq; qd += nw) {
+    const int i0 = qd * kRowsPerWarp;  // kRowsPerWarp consecutive rows of one slice
+    const int s = i0 >> 5;
+    const int o_s = __ldg(a.K.off + s);
+    const int base = o_s + (i0 & 31);
+    const int w = (__ldg(a.K.off + s + 1) - o_s) >> 5;
+    // row operands do not depend on the products: issue them first so their
+    // latency overlaps the matrix stream and the gathers
+    float ko[kRowsPerWarp][H], yo[kRowsPerWarp][H], qv[kRowsPerWarp][H], lo[kRowsPerWarp][H],
+        yb[kRowsPerWarp][H];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const int b = lane + 32 * h, i = i0 + r;
+        ko[r][h] = yo[r][h] = qv[r][h] = lo[r][h] = yb[r][h] = 0.f;
+        if (i < a.m && xg[h]) {
+          const size_t idx = (size_t)i * BP + b;
+          const int p = s_par[b];
+          ko[r][h] = a.Kx[p][idx];
+          yo[r][h] = a.y[p][idx];
+          qv[r][h] = a.qf[idx];
+          if (i >= a.m_eq) lo[r][h] = a.ylf[idx];
+          if (s_pw[b] != 0.f) yb[r][h] = a.ybar[idx];
+        }
+      }
+    float acc[kRowsPerWarp][H];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+      for (int h = 0; h < H; ++h) acc[r][h] = 0.f;
+    // entry k of the group's rows: kRowsPerWarp adjacent slots (16 B aligned:
+    // slice offsets are multiples of 32 and i0 of kRowsPerWarp)
+#pragma unroll 2
     for (int k = 0; k < w; ++k) {
-      const int c = __ldg(a.K.col + o0 + k * kSlice);
-      const float v = __ldg(a.K.val + o0 + k * kSlice);
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(a.K.col + base + k * kSlice));
+      const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.K.val + base + k * kSlice));
+      const int c[4] = {c4.x, c4.y, c4.z, c4.w};
+      const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          if (xg[h]) acc[r][h] += v[r] * __ldg(xg[h] + (size_t)c[r] * BP);
+    }
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r) {
+      const int i = i0 + r;
+      if (i >= a.m) continue;
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int b = lane + 32 * h;
-        if (s_act[b]) acc[h] += v * __ldg(a.x[1 - s_par[b]] + (size_t)c * BP + b);
+        if (!xg[h]) continue;
+        const size_t idx = (size_t)i * BP + b;
+        const int p = s_par[b];
+        float t = qv[r][h] - 2.f * acc[r][h];
+        t = t + ko[r][h];
+        float v = yo[r][h] + s_sigma[b] * t;
+        if (i >= a.m_eq) v = fmaxf(v, lo[r][h]);
+        a.Kx[1 - p][idx] = acc[r][h];
+        a.y[1 - p][idx] = v;
+        if (s_pw[b] != 0.f) a.ybar[idx] = yb[r][h] + s_pw[b] * yo[r][h];
+        const float dy = v - yo[r][h], dk = acc[r][h] - ko[r][h];
+        a_dy2[h] += dy * dy;
+        a_int[h] += dy * dk;
       }
-    }
-#pragma unroll
-    for (int h = 0; h < H; ++h) {
-      const int b = lane + 32 * h;
-      if (!s_act[b]) continue;
-      const size_t idx = (size_t)i * BP + b;
-      const int p = s_par[b];
-      const float ko = a.Kx[p][idx], yo = a.y[p][idx];
-      float t = a.qf[idx] - 2.f * acc[h];
-      t = t + ko;
-      float v = yo + s_sigma[b] * t;
-      if (i >= a.m_eq) v = fmaxf(v, a.ylf[idx]);
-      a.Kx[1 - p][idx] = acc[h];
-      a.y[1 - p][idx] = v;
-      if (s_pw[b] != 0.f) a.ybar[idx] = a.ybar[idx] + s_pw[b] * yo;
-      const float dy = v - yo, dk = acc[h] - ko;
-      a_dy2[h] += dy * dy;
-      a_int[h] += dy * dk;
     }
   }
   __shared__ double smem[kBWarps * BP * 2];
@@ -285,42 +328,80 @@ __global__ void __launch_bounds__(kBThreads) kb_adjoint(BArgs<BP> a) {
   float a_dx2[H];
 #pragma unroll
   for (int h = 0; h < H; ++h) a_dx2[h] = 0.f;
-  for (int j = gw; j < a.n; j += nw) {
-    const int s = j >> 5, r = j & 31;
-    const int o0 = __ldg(a.KT.off + s) + r;
-    const int w = (__ldg(a.KT.off + s + 1) - __ldg(a.KT.off + s)) >> 5;
-    float acc[H];
+  // gather base of each lane's instances (null: no new K^T y this attempt)
+  const float* yg[H];
 #pragma unroll
-    for (int h = 0; h < H; ++h) acc[h] = 0.f;
+  for (int h = 0; h < H; ++h) {
+    const int b = lane + 32 * h;
+    yg[h] = s_acc[b] ? a.y[s_par[b]] + b : nullptr;
+  }
+  const int nq = (a.n + kRowsPerWarp - 1) / kRowsPerWarp;
+  for (int qd = gw; qd < nq; qd += nw) {
+    const int j0 = qd * kRowsPerWarp;  // kRowsPerWarp consecutive columns of one slice
+    const int s = j0 >> 5;
+    const int o_s = __ldg(a.KT.off + s);
+    const int base = o_s + (j0 & 31);
+    const int w = (__ldg(a.KT.off + s + 1) - o_s) >> 5;
+    float x0[kRowsPerWarp][H], cv[kRowsPerWarp][H], lv[kRowsPerWarp][H], uv[kRowsPerWarp][H],
+        xb[kRowsPerWarp][H], go[kRowsPerWarp][H];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const int b = lane + 32 * h, j = j0 + r;
+        x0[r][h] = cv[r][h] = lv[r][h] = uv[r][h] = xb[r][h] = go[r][h] = 0.f;
+        if (j < a.n && s_act[b]) {
+          const size_t idx = (size_t)j * BP + b;
+          const int p = s_par[b];
+          x0[r][h] = a.x[p][idx];
+          cv[r][h] = a.cf[idx];
+          lv[r][h] = a.lf[idx];
+          uv[r][h] = a.uf[idx];
+          if (!s_acc[b]) go[r][h] = a.KTy[p][idx];
+          if (s_acc[b] && s_wl[b] != 0.f) xb[r][h] = a.xbar[idx];
+        }
+      }
+    float acc[kRowsPerWarp][H];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+      for (int h = 0; h < H; ++h) acc[r][h] = 0.f;
+#pragma unroll 2
     for (int k = 0; k < w; ++k) {
-      const int c = __ldg(a.KT.col + o0 + k * kSlice);
-      const float v = __ldg(a.KT.val + o0 + k * kSlice);
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(a.KT.col + base + k * kSlice));
+      const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.KT.val + base + k * kSlice));
+      const int c[4] = {c4.x, c4.y, c4.z, c4.w};
+      const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          if (yg[h]) acc[r][h] += v[r] * __ldg(yg[h] + (size_t)c[r] * BP);
+    }
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r) {
+      const int j = j0 + r;
+      if (j >= a.n) continue;
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int b = lane + 32 * h;
-        if (s_acc[b]) acc[h] += v * __ldg(a.y[s_par[b]] + (size_t)c * BP + b);
+        if (!s_act[b]) continue;
+        const size_t idx = (size_t)j * BP + b;
+        const int p = s_par[b];
+        float gval;
+        if (s_acc[b]) {
+          gval = acc[r][h];
+          a.KTy[p][idx] = gval;
+          if (s_wl[b] != 0.f) a.xbar[idx] = xb[r][h] + s_wl[b] * x0[r][h];
+        } else {
+          gval = go[r][h];
+        }
+        float v = x0[r][h] - s_tau[b] * (cv[r][h] - gval);
+        v = fminf(fmaxf(v, lv[r][h]), uv[r][h]);
+        a.x[1 - p][idx] = v;
+        const float d = v - x0[r][h];
+        a_dx2[h] += d * d;
       }
-    }
-#pragma unroll
-    for (int h = 0; h < H; ++h) {
-      const int b = lane + 32 * h;
-      if (!s_act[b]) continue;
-      const size_t idx = (size_t)j * BP + b;
-      const int p = s_par[b];
-      float gval;
-      if (s_acc[b]) {
-        gval = acc[h];
-        a.KTy[p][idx] = gval;
-      } else {
-        gval = a.KTy[p][idx];
-      }
-      const float x0 = a.x[p][idx];
-      if (s_acc[b] && s_wl[b] != 0.f) a.xbar[idx] = a.xbar[idx] + s_wl[b] * x0;
-      float v = x0 - s_tau[b] * (a.cf[idx] - gval);
-      v = fminf(fmaxf(v, a.lf[idx]), a.uf[idx]);
-      a.x[1 - p][idx] = v;
-      const float d = v - x0;
-      a_dx2[h] += d * d;
     }
   }
   __shared__ double smem[kBWarps * BP];
@@ -949,6 +1030,7 @@ struct Batched {
   void* args = nullptr;  // BArgs<BP> host copy
   BInst* inst = nullptr;
   BInst* inst_host = nullptr;
+  int32_t* done_host = nullptr;  // pinned copy of g->all_done (host-loop mode)
   BGlobal* g = nullptr;
   double* part = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -991,7 +1073,8 @@ int setup_batched(Workspace* w, Batched* bt, BArgs<BP>* out) {
     g_err = std::string("batched allocation: ") + cudaGetErrorString(e);
     return PDHG_ERR_NOMEM;
   }
-  if (cudaMallocHost(&bt->inst_host, sizeof(BInst) * BP) != cudaSuccess) {
+  if (cudaMallocHost(&bt->inst_host, sizeof(BInst) * BP) != cudaSuccess ||
+      cudaMallocHost(&bt->done_host, sizeof(int32_t)) != cudaSuccess) {
     g_err = "batched pinned allocation failed";
     return PDHG_ERR_NOMEM;
   }
@@ -1014,8 +1097,14 @@ int setup_batched(Workspace* w, Batched* bt, BArgs<BP>* out) {
   const int sms = w->num_sms;
   // at least ~8 rows per warp, so the per-instance partials of small problems
   // stay few (their final sums sit on the critical path of every attempt)
-  bt->grid_rows = std::max(1, std::min(sms * 4, (int)((w->m + 8 * kBWarps - 1) / (8 * kBWarps))));
-  bt->grid_cols = std::max(1, std::min(sms * 4, (int)((w->n + 8 * kBWarps - 1) / (8 * kBWarps))));
+  // the sweeps are grid-stride loops: one wave of resident blocks
+  int occ_d = 0, occ_a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, kb_dual<BP>, kBThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, kb_adjoint<BP>, kBThreads, 0);
+  occ_d = std::max(occ_d, 1);
+  occ_a = std::max(occ_a, 1);
+  bt->grid_rows = std::max(1, std::min(sms * occ_d, (int)((w->m + 8 * kBWarps - 1) / (8 * kBWarps))));
+  bt->grid_cols = std::max(1, std::min(sms * occ_a, (int)((w->n + 8 * kBWarps - 1) / (8 * kBWarps))));
   bt->grid_kr = std::max(1, std::min(sms * 8, (int)((w->m + 8 * kKktWarps - 1) / (8 * kKktWarps))));
   bt->grid_kc = std::max(1, std::min(sms * 8, (int)((w->n + 8 * kKktWarps - 1) / (8 * kKktWarps))));
   bt->grid_apply = std::max(
@@ -1098,9 +1187,11 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   BArgs<BP> a = *(BArgs<BP>*)bt->args;
   a.B = B;
   a.in_graph = 0;
-  int rc = build_batched_graph<BP>(w, bt, a);
-  if (rc != PDHG_OK) return rc;
   const pdhg_opts& o = w->opts;
+  if (!o.host_loop) {
+    int rc = build_batched_graph<BP>(w, bt, a);
+    if (rc != PDHG_OK) return rc;
+  }
   cudaEventRecord(w->ev[0], s);
   launch_prepare(w, s);
   launch_to_f32(w->K.val64, w->K.val32, w->K.nnz_pad, s);
@@ -1126,10 +1217,25 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   kb_first_primal<BP><<<gv, 256, 0, s>>>(a);
   kb_dx2<BP><<<BP, kBlock, 0, s>>>(a);
   launch_body<BP>(a, bt, s, 1);  // initial KKT_w of every instance
-  cudaError_t e = cudaGraphLaunch(bt->exec, s);
-  if (e != cudaSuccess) {
-    g_err = std::string("batched graph launch: ") + cudaGetErrorString(e);
-    return PDHG_ERR_CUDA;
+  if (o.host_loop) {
+    // the graph body's kernels launched from the host (profilers cannot see
+    // kernels inside a graph with conditional nodes); one wait per check
+    for (;;) {
+      launch_body<BP>(a, bt, s, 0);
+      if (cudaMemcpyAsync(bt->done_host, &bt->g->all_done, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        g_err = std::string("batched host loop: ") + cudaGetErrorString(cudaGetLastError());
+        return PDHG_ERR_CUDA;
+      }
+      if (*bt->done_host) break;
+    }
+  } else {
+    cudaError_t e = cudaGraphLaunch(bt->exec, s);
+    if (e != cudaSuccess) {
+      g_err = std::string("batched graph launch: ") + cudaGetErrorString(e);
+      return PDHG_ERR_CUDA;
+    }
   }
   kb_output<BP><<<gv, 256, 0, s>>>(a, w->perm_col, w->perm_row, w->Dc, w->Dr, x_out, y_out);
   cudaEventRecord(w->ev[1], s);
@@ -1187,6 +1293,7 @@ void release_batched(Workspace* w) {
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->graph) cudaGraphDestroy(bt->graph);
   if (bt->inst_host) cudaFreeHost(bt->inst_host);
+  if (bt->done_host) cudaFreeHost(bt->done_host);
   for (void* p : bt->allocs) cudaFree(p);
   if (bt->args) {
     if (bt->BP == 64)
