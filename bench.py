@@ -51,6 +51,13 @@ def parse():
                    help="seconds cap of each time-to-tolerance solve (0 = skip)")
     p.add_argument("--cpu-attempts", type=int, default=64, help="oracle attempts of the CPU sample")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--kernel-variant", type=int, default=-1,
+                   help="force a per-attempt kernel variant (0 pipelined, 1, 2, 4) for profiling")
+    p.add_argument("--kernel-grid", type=int, default=0, help="force the per-attempt kernels' grid")
+    p.add_argument("--nodes-workload", default="uc6049_g850_T48_slack",
+                   help="shared LP of the batched node relaxations")
+    p.add_argument("--nodes-attempts", type=int, default=640,
+                   help="attempts per node of the batched-vs-sequential node throughput (0: skip)")
     p.add_argument("--host-loop", action="store_true",
                    help="launch the per-check bodies from the host instead of one CUDA graph "
                         "(same kernels; profilers cannot see kernels inside conditional graphs)")
@@ -177,6 +184,48 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- our arm
+def node_throughput(args, dev, stream, pdhg):
+    """64 node LPs of one shared K (seeded commitment fixings) advanced by the
+    same number of attempts, batched in one pdhg_solve_batched call and as one
+    node alone: node-attempts per second of both (device time, CUDA events)."""
+    import torch
+    from paper_2512_06715_gb300.instances import node_fixings, workload
+
+    inst = workload(args.nodes_workload)
+    B, K = 64, args.nodes_attempts
+    l_np, u_np = node_fixings(inst, B)
+    l_b = torch.as_tensor(l_np, device=dev)
+    u_b = torch.as_tensor(u_np, device=dev)
+    o = pdhg.default_opts(precision="mixed", max_iters=K, tol=1e-12, time_limit_s=600.0,
+                          host_loop=int(args.host_loop), autotune=int(not args.no_autotune))
+
+    def event_time(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3, out
+
+    wb = pdhg.Workspace.from_instance(inst, o, device=dev)
+    wb.solve_batched(l_b, u_b, want_y=False)  # allocations, graph
+    tb, (_, _, rb) = event_time(lambda: wb.solve_batched(l_b, u_b, want_y=False))
+    node_att = sum(r["iterations"] for r in rb)
+    wb.close()
+    w1 = pdhg.Workspace(inst.row_ptr, inst.col, inst.val, inst.c, l_np[0], u_np[0], inst.q, inst.m_eq, o,
+                        device=dev)
+    w1.solve()
+    t1, (_, _, r1) = event_time(lambda: w1.solve())
+    w1.close()
+    nb = node_att / tb
+    ns = r1["iterations"] / t1
+    return {"workload": args.nodes_workload, "n": inst.n, "m": inst.m, "nnz": inst.nnz, "nodes": B,
+            "attempts_per_node": K, "batched_node_attempts_per_s": nb, "sequential_node_attempts_per_s": ns,
+            "ratio": nb / ns, "batched_ms_per_attempt": tb / max(r["iterations"] for r in rb) * 1e3,
+            "note": "node LPs/s = node-attempts/s / attempts per node; equal attempt budgets per node"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -198,7 +247,8 @@ def run_ours(args):
 
     def opts(prec, attempts, tol=1e-8, tl=600.0):
         return pdhg.default_opts(precision=prec, max_iters=attempts, tol=tol, time_limit_s=tl,
-                                 host_loop=int(args.host_loop), autotune=int(not args.no_autotune))
+                                 host_loop=int(args.host_loop), autotune=int(not args.no_autotune),
+                                 kernel_variant=args.kernel_variant, kernel_grid=args.kernel_grid)
 
     ws = pdhg.Workspace.from_instance(inst, opts("mixed", args.attempts), device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
@@ -297,6 +347,8 @@ def run_ours(args):
                          "cap_s": args.ttt_limit, "attempts": r["iterations"],
                          "attempts_per_s": r["iterations"] / r["solve_seconds"]}
 
+    nodes = node_throughput(args, dev, stream, pdhg) if args.nodes_attempts > 0 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         gbs, dt = cpu_oracle_gbs(inst, args.cpu_attempts)
@@ -315,6 +367,7 @@ def run_ours(args):
             "attempts_per_s": {"mixed": att32 / sec_per_step, "fp64": att64 / (t64 / max(1, args.steps // 2))},
             "fp64_gbs": fp64_gbs,
             "time_to_tolerance": ttt,
+            "node_lps": nodes,
             "roofline": roofline,
             "gpu_launches": launches,
             "kernel_tuning": ws.tuning(),

@@ -92,9 +92,15 @@ typedef struct pdhg_opts {
   double step_growth_exp;    /* ... (1+(k+1)^-0.6) eta) (0.6)                         */
   int32_t ruiz_iters;       /* Ruiz l_inf passes (10)                                 */
   int32_t pock_chambolle;   /* 1: one Pock-Chambolle alpha=1 pass (1)                 */
-  double ir_first_tol;      /* mixed: rel_kkt target of the first FP32 round (1e-4)   */
-  double ir_reduction;      /* mixed: per-round reduction of rel_kkt (0.1)            */
-  int32_t ir_max_rounds;    /* mixed: refinement rounds after the first (1000)        */
+  double ir_reduction;      /* mixed: a refinement round ends at the first restart
+                               whose candidate has rel_kkt <= ir_reduction x that of
+                               the round's starting point (or <= tol); the candidate
+                               is folded into x*, y* in FP64 (0.5)                    */
+  double ir_force_reduction; /* mixed: a check whose better candidate is at or below
+                               this factor x the round start's rel_kkt restarts there
+                               (ending the round) even if the restart rule would not
+                               (0.1; <= ir_reduction)                                  */
+  int32_t ir_max_rounds;    /* mixed: refinement rounds after the first (100000)      */
   int32_t trace;            /* 1: record per-attempt/per-check trace (testing) (0)    */
   double fixed_eta;         /* > 0: constant steps eta/omega, no restarts (0)         */
   double fixed_omega;       /* primal weight in fixed-step mode                       */
@@ -109,6 +115,13 @@ typedef struct pdhg_opts {
                                at the first solve of each precision and keep the
                                fastest; 0: fixed defaults (1)                         */
   volatile int32_t *cancel_flag; /* host-mapped int polled at every check, or NULL    */
+  int32_t kernel_variant;   /* -1: the autotuner decides, variant 1 when autotune is 0;
+                               0, 1, 2, 4: that variant of both per-attempt kernels,
+                               as reported by pdhg_get_tuning, with the default grid;
+                               read at the first solve of each precision; default -1 */
+  int32_t kernel_grid;      /* > 0: blocks of both per-attempt kernels, overriding the
+                               autotuner's grid; small grids make each warp sweep
+                               many slices; 0: default or autotuned; default 0       */
 } pdhg_opts;
 
 /* Outcome of one solve (host struct written by the library). */
@@ -223,8 +236,11 @@ int pdhg_get_trace(void *ws, double *attempts, int64_t cap_a, double *checks, in
                    int64_t *n_a, int64_t *n_c);
 
 /* Launch configuration chosen for the per-attempt kernels, host int32 [8]:
- * FP64 {dual unroll, dual grid, adjoint unroll, adjoint grid}, then FP32
- * (zeros for a precision not yet solved). */
+ * FP64 {dual unroll, dual grid, adjoint unroll, adjoint grid}, then FP32.
+ * unroll 1, 2, 4: 32-row slices a warp sweeps together; 0: one slice per warp,
+ * software pipelined (the next slice's first entries and row operands are
+ * loaded while the current slice's gathers are in flight).  A precision not yet
+ * solved reports unroll -1 and grid 0. */
 int pdhg_get_tuning(void *ws, int32_t *cfg);
 
 /* Launch the two per-attempt kernels of `precision` `reps` times each on

@@ -56,7 +56,7 @@ struct DevState {
   int32_t best_is_avg, numeric;
   double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
   // targets and limits
-  double tol, round_target;
+  double tol, round_target, ir_red, round_force, ir_force;
   int64_t max_k, max_checks;
   uint64_t t_start, t_limit_ns;
   double t_tol[3];
@@ -68,15 +68,13 @@ struct DevState {
   int32_t art_total; // artificial restart against attempts of all rounds
   int32_t trace_on;
   int64_t trace_cap_a, trace_cap_c, n_trace_a, n_trace_c;
-  // refinement-round best point (mixed mode): snapshot + stall detection
-  double round_best;
-  int64_t checks_since_best;
-  int64_t stall_min_checks;  // 0 disables the stall rule (plain FP64 solves)
-  int32_t save_best, save_avg;
-  double save_div;
+  // refinement rounds (mixed mode): a restart whose candidate meets
+  // round_target ends the round instead of moving the iterate
+  int32_t refine;
   // norms of the unscaled data and refinement scalars
   double qnorm, cnorm;
   double inv_dp, inv_dd;      // 1/Delta_P, 1/Delta_D
+  double gap_w;               // Delta of round 0 / Delta of this round (weights the gap in KKT_w)
   double const_p, const_d;    // c~^T x*, q~^T y*
   // last-block counters of the reducing kernels
   uint32_t counter;
@@ -94,8 +92,6 @@ struct IterArgs {
   T* ybar;
   T* xa;    // anchors (last restart point)
   T* ya;
-  T* xs;    // snapshot of the round's best point (mixed mode)
-  T* ys;
   const T* c;
   const T* l;
   const T* u;
@@ -185,6 +181,71 @@ __device__ __forceinline__ void final_sum(const double* partials, int nblocks, d
   block_sum<NV>(v, smem);
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = v[k];
+}
+
+// The same last-block reduction with the partials kept in the iterate type T
+// up to the final total: for T = float no FP64 instruction runs per warp (a
+// warp-wide FP64 add holds GB300's narrow FP64 pipe for tens of cycles, which
+// the per-attempt kernels would pay at every block's end).  The partials
+// buffer is reused as T storage.
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NV, class T>
+__device__ __forceinline__ void block_sum_t(T (&v)[NV], T* smem /* [kWarps*NV] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum_t<T>(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[wid * NV + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      T s = 0;
+      for (int w = 0; w < kWarps; ++w) s += smem[w * NV + k];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <int NV, class T>
+__device__ __forceinline__ bool publish_partials_t(T (&v)[NV], double* partials, uint32_t* counter) {
+  __shared__ T smem_t[kWarps * NV];
+  __shared__ int last_t;
+  block_sum_t<NV, T>(v, smem_t);
+  if (threadIdx.x == 0) {
+    T* pt = reinterpret_cast<T*>(partials);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) pt[(size_t)blockIdx.x * NV + k] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    last_t = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last_t != 0;
+}
+
+// Fixed-order total of the T partials; valid in thread 0, returned in FP64.
+template <int NV, class T>
+__device__ __forceinline__ void final_sum_t(const double* partials, int nblocks, double (&out)[NV]) {
+  __shared__ T smem_f[kWarps * NV];
+  const T* pt = reinterpret_cast<const T*>(partials);
+  T v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __ldcg(pt + (size_t)b * NV + k);
+  block_sum_t<NV, T>(v, smem_f);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = (double)v[k];
 }
 
 // (k+1)^(-e) of the step-size rule in FP32 (relative error ~1e-6): an FP64

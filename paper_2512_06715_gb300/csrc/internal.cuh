@@ -32,8 +32,6 @@ struct IterBufs {
   T* ybar = nullptr;
   T* xa = nullptr;
   T* ya = nullptr;
-  T* xs = nullptr;
-  T* ys = nullptr;
   bool allocated = false;
 };
 
@@ -52,18 +50,20 @@ struct RoundInit {
   double eta, omega;       // used when reset_steps
   int32_t reset_steps;     // 1: take eta/omega from the values above
   int32_t first_round;     // 1: restart the clock and the tolerance stamps
-  double tol, round_target;
+  double tol, ir_red, ir_force;
   int64_t max_k, max_checks, k_offset;
   uint64_t t_limit_ns;
   double inv_dp, inv_dd;
+  double gap_w;  // Delta_0 / Delta: keeps KKT_w's gap term in round-0 units
   int32_t fixed, trace_on, art_total;
   int64_t trace_cap_a, trace_cap_c;
-  int64_t stall_min_checks;
+  int32_t refine;  // 1: refinement rounds (mixed precision)
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
 };
 
 // Launch configuration of the two per-attempt kernels of one precision:
-// slices in flight per warp (unroll) and grid size, picked by timing.
+// variant (unroll: 1, 2, 4 slices per warp, 0 software-pipelined) and grid
+// size, picked by timing.
 struct Tune {
   int unroll_dual = 1, grid_dual = 0, unroll_adj = 1, grid_adj = 0;
   bool done = false;

@@ -78,8 +78,6 @@ IterArgs<T> make_args(Workspace* w) {
   a.ybar = b->ybar;
   a.xa = b->xa;
   a.ya = b->ya;
-  a.xs = b->xs;
-  a.ys = b->ys;
   a.n = (int32_t)w->n;
   a.m = (int32_t)w->m;
   a.m_eq = (int32_t)w->m_eq;
@@ -122,8 +120,6 @@ static int alloc_bufs(Workspace* w, IterBufs<T>* b) {
   DALLOC(b->ybar, w->m);
   DALLOC(b->xa, w->n);
   DALLOC(b->ya, w->m);
-  DALLOC(b->xs, w->n);
-  DALLOC(b->ys, w->m);
   b->allocated = true;
   return PDHG_OK;
 }
@@ -155,31 +151,36 @@ static void run_adjoint(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   launch_adjoint<T>(a, t.grid_adj, s, t.unroll_adj);
 }
 
-// Picks, by timing on this workspace's matrix, the slices in flight per warp
-// (1, 2, 4) and the grid size (2 to 8 blocks per SM) of each per-attempt
-// kernel.  The candidate launches run real attempts on scratch state; the
+// Picks, by timing on this workspace's matrix, the variant (1, 2 or 4 slices
+// a warp sweeps together, or 0: the software-pipelined single-slice form) and
+// the grid size (2 to 8 blocks per SM) of each per-attempt kernel.  The candidate launches run real attempts on scratch state; the
 // caller re-initialises the iterates afterwards.
 template <class T>
 static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   const int pi = sizeof(T) == 8 ? 0 : 1;
   Tune& t = w->tune[pi];
   if (t.done) return PDHG_OK;
-  t.unroll_dual = t.unroll_adj = 1;
+  const int fixed_variant = w->opts.kernel_variant;
+  t.unroll_dual = t.unroll_adj = fixed_variant >= 0 ? fixed_variant : 1;
   t.grid_dual = w->grid_k;
   t.grid_adj = w->grid_kt;
-  if (!w->opts.autotune) {
+  if (!w->opts.autotune || fixed_variant >= 0) {
+    if (w->opts.kernel_grid > 0) t.grid_dual = t.grid_adj = w->opts.kernel_grid;
     t.done = true;
     return PDHG_OK;
   }
-  const int unrolls[3] = {1, 2, 4};
+  // 1, 2, 4: slices a warp sweeps together; 0: one slice per warp, software
+  // pipelined (the next slice's first entries and row operands load early)
+  const int unrolls[4] = {1, 2, 4, 0};
   const int bps[5] = {2, 3, 4, 6, 8};
   for (int which = 0; which < 2; ++which) {
     const int nsl = which == 0 ? w->K.nslices : w->KT.nslices;
     float best = 1e30f;
     int bu = 1, bg = which == 0 ? w->grid_k : w->grid_kt;
-    for (int ui = 0; ui < 3; ++ui) {
+    for (int ui = 0; ui < 4; ++ui) {
       const int U = unrolls[ui];
-      const int need = (nsl + kWarps * U - 1) / (kWarps * U);
+      const int Us = U > 0 ? U : 1;
+      const int need = (nsl + kWarps * Us - 1) / (kWarps * Us);
       for (int bi = 0; bi < 5; ++bi) {
         int g = std::min(w->num_sms * bps[bi], std::min(need, kMaxBlocks));
         if (g < 1) g = 1;
@@ -215,6 +216,7 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
       t.grid_adj = bg;
     }
   }
+  if (w->opts.kernel_grid > 0) t.grid_dual = t.grid_adj = w->opts.kernel_grid;
   CK(cudaGetLastError());
   t.done = true;
   return PDHG_OK;
@@ -275,11 +277,15 @@ static int validate_opts(const pdhg_opts* o) {
     return fail(PDHG_ERR_UNSUPPORTED, "opts: check_every must be 64");
   if (o->ruiz_iters < 0 || o->ruiz_iters > 100)
     return fail(PDHG_ERR_INVALID_ARG, "opts: ruiz_iters out of range");
-  if (o->ir_max_rounds < 0 || !(o->ir_first_tol > 0.0) || !(o->ir_reduction > 0.0) ||
-      !(o->ir_reduction < 1.0))
+  if (o->ir_max_rounds < 0 || !(o->ir_reduction > 0.0) || !(o->ir_reduction < 1.0) ||
+      !(o->ir_force_reduction > 0.0) || !(o->ir_force_reduction <= o->ir_reduction))
     return fail(PDHG_ERR_INVALID_ARG, "opts: refinement settings out of range");
   if (o->fixed_eta < 0.0 || (o->fixed_eta > 0.0 && !(o->fixed_omega > 0.0)))
     return fail(PDHG_ERR_INVALID_ARG, "opts: fixed_eta needs fixed_omega > 0");
+  if (o->kernel_variant < -1 || o->kernel_variant > 4 || o->kernel_variant == 3)
+    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2 or 4");
+  if (o->kernel_grid < 0 || o->kernel_grid > kMaxBlocks)
+    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_grid out of range");
   return PDHG_OK;
 }
 
@@ -333,9 +339,9 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
   const bool fixed = o.fixed_eta > 0.0;
   int64_t k_done = 0, accepted = 0, restarts = 0, checks = 0;
   // kernels launched by this call: preparation (8 + 4 per rescaling pass),
-  // FP32 copies, then per round: correction build 4, state 1, init vectors 3,
+  // FP32 copies, then per round: correction build 4, state 1, init vectors 2,
   // first primal step 1, initial check 3, one 64-attempt body (2 per attempt +
-  // a 5-kernel check) per executed check, accumulate 1; output 1.
+  // a 4-kernel check) per executed check, accumulate 1; output 1.
   const int passes = o.ruiz_iters + (o.pock_chambolle ? 1 : 0);
   int64_t launches = 8 + 4 * passes + (mixed ? 2 : 0) + 1;
   // Bound/objective rescaling is round 0 of the refinement form: the solver
@@ -351,7 +357,6 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     omega0 = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;
   }
   double dp = dp0, dd = dd0;
-  double target = mixed ? std::max(o.tol, o.ir_first_tol) : o.tol;
   int status = 0;
   int rounds = 0;
   IterArgs<T> a = make_args<T>(w);
@@ -364,18 +369,20 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     ri.art_total = o.artificial_total ? 1 : 0;
     ri.first_round = (r == 0);
     ri.tol = o.tol;
-    ri.round_target = target;
+    ri.ir_red = o.ir_reduction;
+    ri.ir_force = o.ir_force_reduction;
     ri.max_k = o.max_iters - k_done;
     ri.max_checks = (ri.max_k + kCheckEvery - 1) / kCheckEvery + 1;
     ri.k_offset = k_done;
     ri.t_limit_ns = (uint64_t)(o.time_limit_s * 1e9);
     ri.inv_dp = 1.0 / dp;
     ri.inv_dd = 1.0 / dd;
+    ri.gap_w = dp0 / dp;
     ri.fixed = fixed ? 1 : 0;
     ri.trace_on = o.trace ? 1 : 0;
     ri.trace_cap_a = w->trace_cap_a;
     ri.trace_cap_c = w->trace_cap_c;
-    ri.stall_min_checks = mixed ? 100 : 0;
+    ri.refine = mixed ? 1 : 0;
     ri.beta_suff = o.beta_sufficient;
     ri.beta_nec = o.beta_necessary;
     ri.beta_art = o.beta_artificial;
@@ -418,13 +425,13 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     accepted += h.accepted;
     restarts += h.restarts;
     checks += h.checks;
-    launches += 4 + 1 + 3 + 1 + 3 + h.checks * (2 * kCheckEvery + 5) + 1;
+    launches += 4 + 1 + 2 + 1 + 3 + h.checks * (2 * kCheckEvery + 4) + 1;
     rounds = r;
     status = h.status;
     if (h.status != 0) break;  // optimal or a limit
-    // round target met: refine
+    // the round ended at a restart that met its target: refine from that
+    // candidate (the device sets the next round's target at its first check)
     const double rel = std::max(h.rel_kkt, 1e-300);
-    target = std::max(o.tol, o.ir_reduction * rel);
     // Delta_P / Delta_D grow by 1/rel_kkt relative to round 0, so their ratio
     // (and with it the meaning of the primal weight) stays the same.
     double scale = 1.0 / rel;
@@ -488,9 +495,9 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->step_growth_exp = 0.6;
   o->ruiz_iters = 10;
   o->pock_chambolle = 1;
-  o->ir_first_tol = 1e-4;
-  o->ir_reduction = 0.1;
-  o->ir_max_rounds = 1000;
+  o->ir_reduction = 0.5;
+  o->ir_force_reduction = 0.1;
+  o->ir_max_rounds = 100000;
   o->trace = 0;
   o->fixed_eta = 0.0;
   o->fixed_omega = 0.0;
@@ -499,6 +506,8 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->host_loop = 0;
   o->autotune = 1;
   o->cancel_flag = nullptr;
+  o->kernel_variant = -1;
+  o->kernel_grid = 0;
   return PDHG_OK;
 }
 
@@ -762,9 +771,9 @@ extern "C" int pdhg_get_tuning(void* ws, int32_t* cfg) {
   Workspace* w = (Workspace*)ws;
   for (int p = 0; p < 2; ++p) {
     const Tune& t = w->tune[p];
-    cfg[4 * p + 0] = t.done ? t.unroll_dual : 0;
+    cfg[4 * p + 0] = t.done ? t.unroll_dual : -1;
     cfg[4 * p + 1] = t.done ? t.grid_dual : 0;
-    cfg[4 * p + 2] = t.done ? t.unroll_adj : 0;
+    cfg[4 * p + 2] = t.done ? t.unroll_adj : -1;
     cfg[4 * p + 3] = t.done ? t.grid_adj : 0;
   }
   return PDHG_OK;

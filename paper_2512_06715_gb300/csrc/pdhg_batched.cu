@@ -45,8 +45,7 @@ struct BInst {
   int32_t done, status, rounds, act;  // act: takes part in the next attempts
   int32_t refine, finalize, cand_avg, pad;
   double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
-  double round_target, round_best;
-  int64_t checks_since_best, round_checks;
+  double round_target, round_force;
   double dp, dd;          // Delta_P, Delta_D of the current round
   double next_scale;      // Delta' / Delta for the refinement step
   double const_p, const_d;
@@ -56,7 +55,7 @@ struct BInst {
 };
 
 struct BGlobal {
-  double tol, red, first_tol;
+  double tol, red, force;
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
   int64_t max_k;
   uint64_t t_start, t_limit_ns;
@@ -279,11 +278,11 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
         const double movement = omega * I.dx2 + dy2 / omega;
         const double interaction = 2.0 * fabs(inter);
         const double eta_max = interaction > 0.0 ? movement / interaction : INFINITY;
-        const int64_t k = I.k + 1;
-        I.k = k;
+        I.k += 1;
         I.k_total += 1;
-        const double eta_next = fmin((1.0 - step_power(k + 1, g->red_exp)) * eta_max,
-                                     (1.0 + step_power(k + 1, g->grow_exp)) * eta);
+        // attempts of all rounds (a refinement round is a change of coordinates)
+        const double eta_next = fmin((1.0 - step_power(I.k_total + 1, g->red_exp)) * eta_max,
+                                     (1.0 + step_power(I.k_total + 1, g->grow_exp)) * eta);
         const int accept = eta <= eta_max;
         if (accept) {
           I.par = 1 - I.par;
@@ -618,24 +617,21 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
         reld[c] = sqrt(rd2u) / (1.0 + g->cnorm);
         relg[c] = fabs(P[c] - D[c]) / (1.0 + fabs(P[c]) + fabs(D[c]));
         rel[c] = fmax(relp[c], fmax(reld[c], relg[c]));
-        gh[c] = (P[c] - D[c]) * I.dp * I.dd;
+        // the correction LP's gap is Delta^2 times the LP's, its residuals
+        // Delta times: weighting the gap by 1/Delta keeps the restart test
+        // what it is for the same point in round 0 (up to a common factor)
+        gh[c] = (P[c] - D[c]) * I.dp;
         kw[c] = sqrt(omega * rp2s[c] + rd2s[c] / omega + gh[c] * gh[c]);
       }
       const bool has_avg = I.wsum > 0.0;
       if (init) {
         I.kkt0 = I.kkt_prev = kw[0];
+        I.round_target = fmax(g->tol, g->red * rel[0]);
+        I.round_force = fmax(g->tol, g->force * rel[0]);
       } else {
         I.checks += 1;
-        I.round_checks += 1;
         I.pending_w = 0.0;
         const int best = (has_avg && rel[1] < rel[0]) ? 1 : 0;
-        const bool improved = rel[best] < I.round_best;
-        if (improved) {
-          I.round_best = rel[best];
-          I.checks_since_best = 0;
-        } else {
-          I.checks_since_best += 1;
-        }
         const uint64_t now = globaltimer_ns();
         const double thr[3] = {1e-4, 1e-6, 1e-8};
         for (int t = 0; t < 3; ++t)
@@ -643,15 +639,13 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
             I.t_tol[t] = (double)(now - g->t_start) * 1e-9;
             I.k_tol[t] = I.k_total;
           }
-        if (improved) {
-          I.rel_p = relp[best];
-          I.rel_d = reld[best];
-          I.rel_gap = relg[best];
-          I.rel_kkt = rel[best];
-          I.pobj = P[best];
-          I.dobj = D[best];
-        }
-        int stop = 0, round_end = 0;
+        I.rel_p = relp[best];
+        I.rel_d = reld[best];
+        I.rel_gap = relg[best];
+        I.rel_kkt = rel[best];
+        I.pobj = P[best];
+        I.dobj = D[best];
+        int stop = 0;
         if (!finite) {
           stop = PDHG_STATUS_NUMERIC;
         } else if (rel[best] <= g->tol) {
@@ -662,9 +656,6 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
           stop = PDHG_STATUS_TIME_LIMIT;
         } else if (a.cancel && *a.cancel) {
           stop = PDHG_STATUS_CANCELLED;
-        } else if (rel[best] <= I.round_target ||
-                   (double)I.checks_since_best >= fmax(100.0, 0.5 * (double)I.round_checks)) {
-          round_end = 1;
         }
         if (stop) {
           I.done = 1;
@@ -672,42 +663,55 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
           I.status = stop;
           I.finalize = 1;
           I.cand_avg = best;
-        } else if (round_end) {
-          // next round: the better candidate of this check becomes part of x*
-          const double relb = fmax(rel[best], 1e-300);
-          const double scale = fmin(1.0 / relb, 1e12);
-          I.refine = 1;
-          I.cand_avg = best;
-          const double f = scale / I.dp;  // Delta_P = Delta_D here
-          I.next_scale = f;
-          I.round_target = fmax(g->tol, g->red * relb);
-          I.rounds += 1;
-          // the new round starts at this candidate: its KKT_w in the new scaling
-          // (residual norms scale by f, the gap by f^2)
-          const double g2 = f * f * gh[best];
-          I.kkt0 = sqrt(omega * f * f * rp2s[best] + f * f * rd2s[best] / omega + g2 * g2);
-          I.kkt_prev = I.kkt0;
         } else {
-          const int to_avg = (has_avg && kw[1] < kw[0]) ? 1 : 0;
+          int to_avg = (has_avg && kw[1] < kw[0]) ? 1 : 0;
           const double kc = kw[to_avg];
-          const int restart = (kc <= g->beta_suff * I.kkt0) ||
-                              (kc <= g->beta_nec * I.kkt0 && kc > I.kkt_prev) ||
-                              ((double)I.since_restart >= g->beta_art * (double)I.k_total);
+          int restart = (kc <= g->beta_suff * I.kkt0) ||
+                        (kc <= g->beta_nec * I.kkt0 && kc > I.kkt_prev) ||
+                        ((double)I.since_restart >= g->beta_art * (double)I.k_total);
           I.kkt_prev = kc;
+          if (!restart && rel[best] <= I.round_force) {
+            restart = 1;  // forced: the round ends at the better candidate
+            to_avg = best;
+          }
           if (restart) {
             const double Dx = sqrt(dxa[to_avg]), Dy = sqrt(dya[to_avg]);
             double om = omega;
             if (Dx > 1e-10 && Dy > 1e-10)
               om = exp(g->omega_smooth * log(Dy / Dx) + (1.0 - g->omega_smooth) * log(omega));
             I.omega = om;
-            I.kkt0 = sqrt(om * rp2s[to_avg] + rd2s[to_avg] / om + gh[to_avg] * gh[to_avg]);
-            I.kkt_prev = I.kkt0;
-            I.avg_div = I.wsum;
-            I.wsum = 0.0;
-            I.since_restart = 0;
+            const double k0 = sqrt(om * rp2s[to_avg] + rd2s[to_avg] / om + gh[to_avg] * gh[to_avg]);
             I.restarts += 1;
-            I.restart_now = 1;
-            I.restart_to_avg = to_avg;
+            if (rel[to_avg] <= I.round_target) {
+              // refinement: this restart ends the round; its candidate joins
+              // x*, y* and the next round restarts from it at x^ = y^ = 0
+              const double relb = fmax(rel[to_avg], 1e-300);
+              const double scale = fmin(1.0 / relb, 1e12);
+              I.refine = 1;
+              I.cand_avg = to_avg;
+              const double f = scale / I.dp;  // Delta_P = Delta_D here
+              I.next_scale = f;
+              I.round_target = fmax(g->tol, g->red * relb);
+              I.round_force = fmax(g->tol, g->force * relb);
+              I.rounds += 1;
+              // the candidate's KKT_w in the new scaling: every term scales by f
+              I.kkt0 = f * k0;
+              I.kkt_prev = I.kkt0;
+              I.rel_p = relp[to_avg];
+              I.rel_d = reld[to_avg];
+              I.rel_gap = relg[to_avg];
+              I.rel_kkt = rel[to_avg];
+              I.pobj = P[to_avg];
+              I.dobj = D[to_avg];
+            } else {
+              I.kkt0 = k0;
+              I.kkt_prev = k0;
+              I.avg_div = I.wsum;
+              I.wsum = 0.0;
+              I.since_restart = 0;
+              I.restart_now = 1;
+              I.restart_to_avg = to_avg;
+            }
           }
         }
       }
@@ -854,9 +858,6 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
           J.w_last = J.pending_w = J.wsum = 0.0;
           J.k = 0;
           J.since_restart = 0;
-          J.round_checks = 0;
-          J.checks_since_best = 0;
-          J.round_best = INFINITY;
           J.restart_now = 0;
         }
       }
@@ -1013,8 +1014,6 @@ __global__ void kb_init_state(BInst* inst, BGlobal* g, int B, int BP, const doub
     I.done = b >= B;
     I.dp = I.dd = 1.0;
     I.next_scale = 1.0;
-    I.round_target = fmax(gin.tol, gin.first_tol);
-    I.round_best = INFINITY;
     I.rel_kkt = INFINITY;
     for (int t = 0; t < 3; ++t) {
       I.t_tol[t] = -1.0;
@@ -1200,7 +1199,7 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   BGlobal gin{};
   gin.tol = o.tol;
   gin.red = o.ir_reduction;
-  gin.first_tol = o.ir_first_tol;
+  gin.force = o.ir_force_reduction;
   gin.beta_suff = o.beta_sufficient;
   gin.beta_nec = o.beta_necessary;
   gin.beta_art = o.beta_artificial;

@@ -124,8 +124,11 @@ __device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, doub
   const double eta_max = interaction > 0.0 ? movement / interaction : INFINITY;
   const int64_t k = st->k + 1;
   st->k = k;
-  double eta_next = fmin((1.0 - step_power(k + 1, st->red_exp)) * eta_max,
-                         (1.0 + step_power(k + 1, st->grow_exp)) * eta);
+  // attempts of all rounds: a refinement round is a change of coordinates,
+  // not a new solve
+  const int64_t kg = st->k_offset + k;
+  double eta_next = fmin((1.0 - step_power(kg + 1, st->red_exp)) * eta_max,
+                         (1.0 + step_power(kg + 1, st->grow_exp)) * eta);
   int accept = eta <= eta_max;
   if (st->fixed) {
     accept = 1;
@@ -175,8 +178,8 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nw = (gridDim.x * kBlock) >> 5;
-  // per-thread partials in the iterate precision (a thread sums a few rows);
-  // FP64 only across threads: FP64 throughput on this GPU is ~1/60 of FP32
+  // partials in the iterate precision up to the block totals (FP64
+  // throughput on this GPU is ~1/60 of FP32); the step rule is a heuristic
   T acc_dy2 = 0, acc_int = 0;
   int ob[U + 1];
   slice_offsets<T, U>(a.K, gw * U, ob);
@@ -220,10 +223,10 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
       }
     }
   }
-  double acc[2] = {(double)acc_dy2, (double)acc_int};
-  if (publish_partials<2>(acc, a.partials, &st->counter)) {
+  T acc[2] = {acc_dy2, acc_int};
+  if (publish_partials_t<2, T>(acc, a.partials, &st->counter)) {
     double tot[2];
-    final_sum<2>(a.partials, gridDim.x, tot);
+    final_sum_t<2, T>(a.partials, gridDim.x, tot);
     if (threadIdx.x == 0) {
       decide_step(st, a, tot[0], tot[1]);
       st->counter = 0;
@@ -287,10 +290,10 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(IterArgs<T> a) {
       }
     }
   }
-  double acc[1] = {(double)acc_dx2};
-  if (publish_partials<1>(acc, a.partials, &st->counter)) {
+  T acc[1] = {acc_dx2};
+  if (publish_partials_t<1, T>(acc, a.partials, &st->counter)) {
     double tot[1];
-    final_sum<1>(a.partials, gridDim.x, tot);
+    final_sum_t<1, T>(a.partials, gridDim.x, tot);
     if (threadIdx.x == 0) {
       st->dx2 = tot[0];
       st->counter = 0;
@@ -298,7 +301,232 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(IterArgs<T> a) {
   }
 }
 
-// x = proj_[l,u](0), y = proj(0), averages and anchors reset; K x and K^T y.
+// ---- software-pipelined variants (one slice per warp) -------------------------
+//
+// A warp sweeps its slices s, s + nw, s + 2 nw, ...  While the gathers of slice
+// s are in flight, the first kStage entries (columns and values) and the row
+// operands of slice s + nw are already loading, and the offsets of s + 2 nw
+// before them: two dependent round trips per slice (matrix from HBM, gathered
+// vector from L2) overlap instead of following each other.  Entries beyond
+// kStage (the long minimum-up/down rows) are read after the gathers.
+
+constexpr int kStage = 4;
+
+template <class T>
+struct SliceStage {
+  int o0, w;          // first slot of this lane, entries per row
+  int c[kStage];
+  T v[kStage];
+};
+
+template <class T>
+__device__ __forceinline__ void stage_slice(const SellView<T>& A, int ob, int oe, int lane,
+                                            SliceStage<T>& g) {
+  g.o0 = ob + lane;
+  g.w = (oe - ob) >> 5;
+#pragma unroll
+  for (int e = 0; e < kStage; ++e) {
+    const bool ok = e < g.w;
+    g.c[e] = ok ? __ldg(A.col + g.o0 + e * kSlice) : 0;
+    g.v[e] = ok ? __ldg(A.val + g.o0 + e * kSlice) : (T)0;
+  }
+}
+
+// Row products of a staged slice with x1 and (if TWO) x2.
+template <class T, bool TWO>
+__device__ __forceinline__ void staged_dot(const SellView<T>& A, const SliceStage<T>& g,
+                                           const T* __restrict__ x1, const T* __restrict__ x2,
+                                           T& acc1, T& acc2) {
+  acc1 = 0;
+  acc2 = 0;
+#pragma unroll
+  for (int e = 0; e < kStage; ++e)
+    if (e < g.w) {
+      acc1 += g.v[e] * __ldg(x1 + g.c[e]);
+      if (TWO) acc2 += g.v[e] * __ldg(x2 + g.c[e]);
+    }
+  for (int k0 = kStage; k0 < g.w; k0 += 4) {
+    int c[4];
+    T v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const bool ok = k0 + e < g.w;
+      c[e] = ok ? __ldg(A.col + g.o0 + (k0 + e) * kSlice) : 0;
+      v[e] = ok ? __ldg(A.val + g.o0 + (k0 + e) * kSlice) : (T)0;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (k0 + e < g.w) {
+        acc1 += v[e] * __ldg(x1 + c[e]);
+        if (TWO) acc2 += v[e] * __ldg(x2 + c[e]);
+      }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_dual_pipe(IterArgs<T> a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  const int p = st->par;
+  const double pw = st->pending_w;
+  const bool has_pw = pw != 0.0;
+  const T pwT = (T)pw;
+  const T sigma = (T)(st->eta * st->omega);
+  const T* __restrict__ xn = a.x[1 - p];
+  const T* __restrict__ xc = a.x[p];
+  const T* __restrict__ yc = a.y[p];
+  T* __restrict__ yn = a.y[1 - p];
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  const int ns = a.K.nslices;
+  T acc_dy2 = 0, acc_int = 0;
+  // stage the warp's first slice; offsets of the second
+  SliceStage<T> cur;
+  T yo, qi, lo, yb;
+  auto row_ops = [&](int s, T& y0, T& q0, T& l0, T& b0) {
+    const int i = s * kSlice + lane;
+    y0 = q0 = l0 = b0 = 0;
+    if (s < ns && i < a.m) {
+      y0 = yc[i];
+      q0 = a.q[i];
+      if (i >= a.m_eq) l0 = dual_floor(a.ylo, i, a.m_eq);
+      if (has_pw) b0 = a.ybar[i];
+    }
+  };
+  {
+    const int s = min(gw, ns);
+    stage_slice<T>(a.K, __ldg(a.K.off + s), __ldg(a.K.off + min(s + 1, ns)), lane, cur);
+    row_ops(gw, yo, qi, lo, yb);
+  }
+  int nb0 = __ldg(a.K.off + min(gw + nw, ns)), nb1 = __ldg(a.K.off + min(gw + nw + 1, ns));
+  for (int s = gw; s < ns; s += nw) {
+    // next slice: entries and row operands; offsets two slices ahead
+    SliceStage<T> nxt;
+    T yo2, qi2, lo2, yb2;
+    stage_slice<T>(a.K, nb0, nb1, lane, nxt);
+    row_ops(s + nw, yo2, qi2, lo2, yb2);
+    nb0 = __ldg(a.K.off + min(s + 2 * nw, ns));
+    nb1 = __ldg(a.K.off + min(s + 2 * nw + 1, ns));
+    T kx, ko;
+    staged_dot<T, true>(a.K, cur, xn, xc, kx, ko);
+    const int i = s * kSlice + lane;
+    if (i < a.m) {
+      T t = qi - (T)2 * kx;
+      t = t + ko;
+      T v = yo + sigma * t;
+      if (i >= a.m_eq) v = max(v, lo);
+      yn[i] = v;
+      if (has_pw) a.ybar[i] = yb + pwT * yo;
+      const T dy = v - yo;
+      acc_dy2 += dy * dy;
+      acc_int += dy * (kx - ko);
+    }
+    cur = nxt;
+    yo = yo2;
+    qi = qi2;
+    lo = lo2;
+    yb = yb2;
+  }
+  T acc[2] = {acc_dy2, acc_int};
+  if (publish_partials_t<2, T>(acc, a.partials, &st->counter)) {
+    double tot[2];
+    final_sum_t<2, T>(a.partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      decide_step(st, a, tot[0], tot[1]);
+      st->counter = 0;
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_adjoint_pipe(IterArgs<T> a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  const int p = st->par;
+  const int acc_last = st->accepted_last;
+  const double wl = st->w_last;
+  const bool upd_avg = acc_last && wl != 0.0;
+  const T wlT = (T)wl;
+  const T tau = (T)(st->eta / st->omega);
+  const T* __restrict__ yc = a.y[p];
+  const T* __restrict__ xc = a.x[p];
+  T* __restrict__ kty = a.KTy[p];
+  T* __restrict__ xn = a.x[1 - p];
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  const int ns = a.KT.nslices;
+  T acc_dx2 = 0;
+  auto col_ops = [&](int s, T& x0, T& c0, T& l0, T& u0, T& b0, T& g0) {
+    const int j = s * kSlice + lane;
+    x0 = c0 = l0 = u0 = b0 = g0 = 0;
+    if (s < ns && j < a.n) {
+      x0 = xc[j];
+      c0 = a.c[j];
+      l0 = a.l[j];
+      u0 = a.u[j];
+      if (upd_avg) b0 = a.xbar[j];
+      if (!acc_last) g0 = kty[j];
+    }
+  };
+  SliceStage<T> cur;
+  cur.w = 0;
+  T x0, cj, lj, uj, xb, g;
+  if (acc_last) {
+    const int s = min(gw, ns);
+    stage_slice<T>(a.KT, __ldg(a.KT.off + s), __ldg(a.KT.off + min(s + 1, ns)), lane, cur);
+  }
+  col_ops(gw, x0, cj, lj, uj, xb, g);
+  int nb0 = 0, nb1 = 0;
+  if (acc_last) {
+    nb0 = __ldg(a.KT.off + min(gw + nw, ns));
+    nb1 = __ldg(a.KT.off + min(gw + nw + 1, ns));
+  }
+  for (int s = gw; s < ns; s += nw) {
+    SliceStage<T> nxt;
+    nxt.w = 0;
+    T x2, c2, l2, u2, b2, g2;
+    if (acc_last) {
+      stage_slice<T>(a.KT, nb0, nb1, lane, nxt);
+      nb0 = __ldg(a.KT.off + min(s + 2 * nw, ns));
+      nb1 = __ldg(a.KT.off + min(s + 2 * nw + 1, ns));
+    }
+    col_ops(s + nw, x2, c2, l2, u2, b2, g2);
+    if (acc_last) {
+      T unused;
+      staged_dot<T, false>(a.KT, cur, yc, yc, g, unused);
+    }
+    const int j = s * kSlice + lane;
+    if (j < a.n) {
+      if (acc_last) kty[j] = g;
+      if (upd_avg) a.xbar[j] = xb + wlT * x0;
+      T v = x0 - tau * (cj - g);
+      v = min(max(v, lj), uj);
+      xn[j] = v;
+      const T d = v - x0;
+      acc_dx2 += d * d;
+    }
+    cur = nxt;
+    x0 = x2;
+    cj = c2;
+    lj = l2;
+    uj = u2;
+    xb = b2;
+    g = g2;
+  }
+  T acc[1] = {acc_dx2};
+  if (publish_partials_t<1, T>(acc, a.partials, &st->counter)) {
+    double tot[1];
+    final_sum_t<1, T>(a.partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      st->dx2 = tot[0];
+      st->counter = 0;
+    }
+  }
+}
+
+// x = proj_[l,u](0), y = proj(0), averages and anchors reset; K^T y.
 template <class T>
 __global__ void k_init_vectors(IterArgs<T> a) {
   const int64_t N = a.n > a.m ? a.n : a.m;
@@ -362,7 +590,10 @@ __global__ void k_state_init(DevState* st, RoundInit r, const double* scalars) {
   st->best_is_avg = 0;
   st->numeric = 0;
   st->tol = r.tol;
-  st->round_target = r.round_target;
+  st->ir_red = r.ir_red;
+  st->ir_force = r.ir_force;
+  st->round_force = 0.0;
+  st->round_target = r.tol;
   st->max_k = r.max_k;
   st->max_checks = r.max_checks;
   st->k_offset = r.k_offset;
@@ -391,13 +622,10 @@ __global__ void k_state_init(DevState* st, RoundInit r, const double* scalars) {
   st->cnorm = scalars[3];
   st->inv_dp = r.inv_dp;
   st->inv_dd = r.inv_dd;
+  st->gap_w = r.gap_w > 0.0 ? r.gap_w : 1.0;
   st->const_p = scalars[6];
   st->const_d = scalars[7];
-  st->round_best = INFINITY;
-  st->checks_since_best = 0;
-  st->stall_min_checks = r.stall_min_checks;
-  st->save_best = 0;
-  st->save_avg = 0;
+  st->refine = r.refine;
   st->counter = 0;
   st->counter2 = 0;
 }
@@ -422,6 +650,7 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
 template <class T>
 void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
+    case 0: k_dual_pipe<T><<<grid, kBlock, 0, s>>>(a); break;
     case 2: k_dual<T, 2><<<grid, kBlock, 0, s>>>(a); break;
     case 4: k_dual<T, 4><<<grid, kBlock, 0, s>>>(a); break;
     default: k_dual<T, 1><<<grid, kBlock, 0, s>>>(a); break;
@@ -431,6 +660,7 @@ void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
 template <class T>
 void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
+    case 0: k_adjoint_pipe<T><<<grid, kBlock, 0, s>>>(a); break;
     case 2: k_adjoint<T, 2><<<grid, kBlock, 0, s>>>(a); break;
     case 4: k_adjoint<T, 4><<<grid, kBlock, 0, s>>>(a); break;
     default: k_adjoint<T, 1><<<grid, kBlock, 0, s>>>(a); break;

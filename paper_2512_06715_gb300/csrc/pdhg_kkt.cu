@@ -6,12 +6,17 @@
 // Sec. II.E).  It evaluates, with the FP64 rescaled matrix,
 //   outer (unscaled) measures of the original LP -> termination (rel_kkt)
 //   KKT_w = sqrt(w ||r_p||^2 + ||r_d||^2 / w + gap^2) in the solver's own
-//           (rescaled, refinement-scaled) space           -> restart decision
+//           (rescaled, refinement-scaled) space, the gap weighted back to
+//           round-0 units                                 -> restart decision
 // The iterate is the correction (x^, y^) of a refinement round: the implied
 // point of the original LP is x~ = x* + x^/Delta_P, y~ = y* + y^/Delta_D, so
 //   r_p(original) = (q^ - K~ x^) / Delta_P / Dr,  lambda = (c^ - K~^T y^)/Delta_D,
 //   P = c~^T x^ / Delta_P + c~^T x*,  D = q~^T y^ / Delta_D + q~^T y* + bounds(lambda)
-// A plain FP64 solve is the single round x* = y* = 0, Delta = 1.
+// A plain FP64 solve is the single round x* = y* = 0, Delta = 1.  In mixed
+// precision a round ends at the first restart whose candidate reaches the
+// round's target: the candidate joins x*, y* (FP64) and the next round starts
+// from it at x^ = y^ = 0 with the same step size and primal weight, i.e. the
+// same restart expressed in new coordinates.
 #include "internal.cuh"
 
 namespace ucpdhg {
@@ -182,7 +187,11 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     reld[c] = sqrt(rd2u) / (1.0 + st->cnorm);
     relg[c] = fabs(P[c] - D[c]) / (1.0 + fabs(P[c]) + fabs(D[c]));
     rel[c] = fmax(relp[c], fmax(reld[c], relg[c]));
-    gh[c] = (P[c] - D[c]) * dp * dd;
+    // Correction LP of a refinement round: residuals scale with Delta, the
+    // gap with Delta^2.  Weighting the gap by Delta_0/Delta keeps KKT_w (and
+    // with it the restart decisions) what it is for the same point in round 0,
+    // up to a factor common to the whole round.
+    gh[c] = (P[c] - D[c]) * dp * dd * st->gap_w;
     kw[c] = sqrt(omega * rp2s[c] + rd2s[c] / omega + gh[c] * gh[c]);
   }
   const bool has_avg = st->wsum > 0.0;
@@ -190,6 +199,10 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     st->kkt0 = kw[0];
     st->kkt_prev = kw[0];
     st->best_is_avg = 0;
+    // a refinement round ends at a restart whose candidate improves on the
+    // round's starting point by the factor ir_red
+    st->round_target = st->refine ? fmax(st->tol, st->ir_red * rel[0]) : st->tol;
+    st->round_force = st->refine ? fmax(st->tol, st->ir_force * rel[0]) : 0.0;
     st->rel_p = relp[0];
     st->rel_d = reld[0];
     st->rel_gap = relg[0];
@@ -199,34 +212,15 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     return;
   }
   st->checks += 1;
-  st->save_best = 0;
   st->pending_w = 0.0;  // applied by k_kkt_row
   const int best = (has_avg && rel[1] < rel[0]) ? 1 : 0;
   st->best_is_avg = best;
-  // Plain solves report the last check's better candidate.  Refinement rounds
-  // keep a snapshot of the best point of the round (k_save_best) and report it.
-  const bool snapshot = st->stall_min_checks > 0;
-  bool improved = false;
-  if (snapshot) {
-    improved = rel[best] < st->round_best;
-    if (improved) {
-      st->round_best = rel[best];
-      st->checks_since_best = 0;
-      st->save_best = 1;
-      st->save_avg = best;
-      st->save_div = st->wsum;
-    } else {
-      st->checks_since_best += 1;
-    }
-  }
-  if (!snapshot || improved) {
-    st->rel_p = relp[best];
-    st->rel_d = reld[best];
-    st->rel_gap = relg[best];
-    st->rel_kkt = rel[best];
-    st->pobj = P[best];
-    st->dobj = D[best];
-  }
+  st->rel_p = relp[best];
+  st->rel_d = reld[best];
+  st->rel_gap = relg[best];
+  st->rel_kkt = rel[best];
+  st->pobj = P[best];
+  st->dobj = D[best];
   const uint64_t now = globaltimer_ns();
   const double elapsed = (double)(now - st->t_start) * 1e-9;
   const double thr[3] = {1e-4, 1e-6, 1e-8};
@@ -245,13 +239,9 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     done = 1;
     status = PDHG_STATUS_NUMERIC;
     st->numeric = 1;
-  } else if (rel[best] <= st->round_target) {
+  } else if (rel[best] <= st->tol) {
     done = 1;
-    status = rel[best] <= st->tol ? PDHG_STATUS_OPTIMAL : 0;
-  } else if (snapshot && (double)st->checks_since_best >=
-                             fmax((double)st->stall_min_checks, 0.5 * (double)st->checks)) {
-    done = 1;  // the round stalled: refine from its best point
-    status = 0;
+    status = PDHG_STATUS_OPTIMAL;
   } else if (st->k >= st->max_k || st->checks >= st->max_checks) {
     done = 1;
     status = PDHG_STATUS_ITER_LIMIT;
@@ -271,6 +261,13 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
               ((double)st->since_restart >=
                st->beta_art * (double)(st->art_total ? st->k_offset + st->k : st->k));
     st->kkt_prev = kc;
+    if (st->refine && !restart && rel[best] <= st->round_force) {
+      // the round's error fell far below its start without a restart: restart
+      // at the better candidate so that the round can end there (the FP32
+      // correction would otherwise approach its own rounding floor)
+      restart = 1;
+      to_avg = best;
+    }
     if (restart) {
       const double Dx = sqrt(dxa[to_avg]), Dy = sqrt(dya[to_avg]);
       double om = omega;
@@ -281,10 +278,26 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
       st->omega = om;
       st->kkt0 = sqrt(om * rp2s[to_avg] + rd2s[to_avg] / om + gh[to_avg] * gh[to_avg]);
       st->kkt_prev = st->kkt0;
-      st->avg_div = st->wsum;
-      st->wsum = 0.0;
-      st->since_restart = 0;
       st->restarts += 1;
+      if (st->refine && rel[to_avg] <= st->round_target) {
+        // Refinement: this restart ends the round.  Its candidate joins x*, y*
+        // in FP64 and the next round restarts from it at x^ = y^ = 0 with the
+        // same eta and omega, which is the same restart in new coordinates.
+        done = 1;
+        status = 0;
+        restart = 0;
+        st->best_is_avg = to_avg;
+        st->rel_p = relp[to_avg];
+        st->rel_d = reld[to_avg];
+        st->rel_gap = relg[to_avg];
+        st->rel_kkt = rel[to_avg];
+        st->pobj = P[to_avg];
+        st->dobj = D[to_avg];
+      } else {
+        st->avg_div = st->wsum;
+        st->wsum = 0.0;
+        st->since_restart = 0;
+      }
     }
   }
   st->restart_now = restart;
@@ -307,22 +320,6 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     st->n_trace_c = t + 1;
   }
   if (a.in_graph) cudaGraphSetConditional(a.cond, done ? 0u : 1u);
-}
-
-// Copies the candidate k_control marked as the round's best (refinement rounds).
-template <class T>
-__global__ void k_save_best(IterArgs<T> a) {
-  DevState* st = a.st;
-  if (!st->save_best) return;
-  const int p = st->par;
-  const int avg = st->save_avg;
-  const double div = st->save_div;
-  const int64_t N = a.n > a.m ? a.n : a.m;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    if (t < a.n) a.xs[t] = avg ? (T)((double)a.xbar[t] / div) : a.x[p][t];
-    if (t < a.m) a.ys[t] = avg ? (T)((double)a.ybar[t] / div) : a.y[p][t];
-  }
 }
 
 // Moves the iterate to the restart candidate, resets anchors and averages, and
@@ -378,19 +375,16 @@ __global__ void k_accumulate(IterArgs<T> a, double* x_star, double* y_star) {
   DevState* st = a.st;
   const int p = st->par;
   const int avg = st->best_is_avg;
-  const bool snapshot = st->stall_min_checks > 0;
   const double wsum = st->wsum, inv_dp = st->inv_dp, inv_dd = st->inv_dd;
   const int64_t N = a.n > a.m ? a.n : a.m;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
     if (t < a.n) {
-      const double xv = snapshot ? (double)a.xs[t]
-                                 : (avg ? (double)a.xbar[t] / wsum : (double)a.x[p][t]);
+      const double xv = avg ? (double)a.xbar[t] / wsum : (double)a.x[p][t];
       x_star[t] = x_star[t] + xv * inv_dp;
     }
     if (t < a.m) {
-      const double yv = snapshot ? (double)a.ys[t]
-                                 : (avg ? (double)a.ybar[t] / wsum : (double)a.y[p][t]);
+      const double yv = avg ? (double)a.ybar[t] / wsum : (double)a.y[p][t];
       y_star[t] = y_star[t] + yv * inv_dd;
     }
   }
@@ -480,10 +474,7 @@ void launch_check(const IterArgs<T>& a, int grid_k, int grid_kt, int init, cudaS
   k_kkt_row<T><<<grid_k, kBlock, 0, s>>>(a);
   k_kkt_col<T><<<grid_kt, kBlock, 0, s>>>(a);
   k_control<T><<<1, kBlock, 0, s>>>(a, grid_k, grid_kt, init);
-  if (!init) {
-    k_save_best<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a);
-    k_restart_apply<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a);
-  }
+  if (!init) k_restart_apply<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a);
 }
 
 template <class T>

@@ -86,14 +86,18 @@ def test_spmv_and_scaling_parity(shape):
     ws.close()
 
 
-def test_fixed_step_iterates_match_oracle(tiny24):
+@pytest.mark.parametrize("variant,grid", [(-1, 0), (1, 3), (2, 3), (4, 2), (0, 0), (0, 3)])
+def test_fixed_step_iterates_match_oracle(tiny24, variant, grid):
     """Constant steps, no restarts: iterates after 128 attempts agree with the
-    oracle to 1e-10 relative."""
+    oracle to 1e-10 relative, for every variant of the per-attempt kernels
+    (1, 2, 4 slices per warp; 0 software pipelined) with the default grid and
+    with 2-3 blocks, where each warp sweeps many slices and the ragged last one."""
     inst, lp = tiny24
     slp, _, _ = rescale(lp)
     eta = 0.9 / np.abs(slp.K.data).max()
     omega = np.linalg.norm(slp.c) / np.linalg.norm(slp.q)
-    ws = _ws(inst, fixed_eta=eta, fixed_omega=omega, max_iters=128, tol=1e-30)
+    ws = _ws(inst, fixed_eta=eta, fixed_omega=omega, max_iters=128, tol=1e-30,
+             kernel_variant=variant, kernel_grid=grid)
     x, y, r = ws.solve()
     x, y = x.cpu().numpy(), y.cpu().numpy()
     ref = pdhg_solve(lp, fixed=dict(eta=eta, omega=omega), stop_after=128)
@@ -147,6 +151,21 @@ def test_solve_tiny_matches_oracle(tiny24, tiny24_oracle, precision):
     assert abs(chk.primal_obj - ref.primal_obj) <= 1e-6 * abs(ref.primal_obj)
     assert max_violation(lp, x) <= 1e-7 * max(1.0, np.abs(lp.q).max())
     assert r["time_to_tol"][0] > 0 and r["time_to_tol"][2] >= r["time_to_tol"][0]
+
+
+@pytest.mark.parametrize("variant", [0, 2, 4])
+def test_mixed_solve_kernel_variants(tiny24, tiny24_oracle, variant):
+    """The FP32 kernel variants, on 3 blocks (many slices per warp), solve the
+    tiny LP to rel-KKT 1e-8 with the oracle's objective."""
+    inst, lp = tiny24
+    ws = _ws(inst, precision="mixed", tol=1e-8, kernel_variant=variant, kernel_grid=3)
+    x, y, r = ws.solve()
+    x = x.cpu().numpy()
+    assert r["status_name"] == "optimal", r
+    assert ws.tuning()["fp32"]["unroll_dual"] == variant
+    assert abs(kkt(lp, x, y.cpu().numpy()).primal_obj - tiny24_oracle.primal_obj) <= \
+        1e-6 * abs(tiny24_oracle.primal_obj)
+    assert max_violation(lp, x) <= 1e-7 * max(1.0, np.abs(lp.q).max())
 
 
 @pytest.mark.parametrize("seed", [0, 1])
