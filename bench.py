@@ -129,15 +129,16 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def dram_traffic_record(kernel_src: Path):
+def dram_traffic_record(kernel_src: Path, kernel: str):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+    valid only for the same kernel variant and while its source is unchanged
+    since the capture."""
     rec = ROOT / "profiles" / "dram_traffic.json"
     if not rec.exists():
         return None
     d = json.loads(rec.read_text())
     h = hashlib.sha256(kernel_src.read_bytes()).hexdigest()[:16]
-    if d.get("kernel_source_sha256_16") != h:
+    if d.get("kernel_source_sha256_16") != h or d.get("kernel") != kernel:
         return None
     return d
 
@@ -302,8 +303,10 @@ def run_ours(args):
     tk = ws.time_kernels(pdhg.PREC_MIXED, reps=20)
     achieved = tk["bytes_dual"] / (tk["ms_dual"] * 1e-3) / 1e9
     peaks = measured_peaks()
-    traffic = dram_traffic_record(ROOT / "paper_2512_06715_gb300" / "csrc" / "pdhg_kernels.cu")
-    roofline = {"bound": "hbm", "kernel": "k_dual<float> (K x' + projected dual step)",
+    u_dual = ws.tuning()["fp32"]["unroll_dual"]
+    kname = "k_dual_pipe<float>" if u_dual == 0 else f"k_dual<float, {u_dual}>"
+    traffic = dram_traffic_record(ROOT / "paper_2512_06715_gb300" / "csrc" / "pdhg_kernels.cu", kname)
+    roofline = {"bound": "hbm", "kernel": kname + " (K x' + projected dual step)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (burst)",
                 "traffic": (traffic["bytes_per_launch"] if traffic else None),

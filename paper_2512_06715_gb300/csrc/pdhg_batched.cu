@@ -675,7 +675,9 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
             to_avg = best;
           }
           if (restart) {
-            const double Dx = sqrt(dxa[to_avg]), Dy = sqrt(dya[to_avg]);
+            // distances in round-0 units (the correction coordinates are Delta
+            // times larger): the "too small to update omega" test stays fixed
+            const double Dx = sqrt(dxa[to_avg]) / I.dp, Dy = sqrt(dya[to_avg]) / I.dd;
             double om = omega;
             if (Dx > 1e-10 && Dy > 1e-10)
               om = exp(g->omega_smooth * log(Dy / Dx) + (1.0 - g->omega_smooth) * log(omega));
@@ -765,7 +767,7 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
           a.qh[idx] = qn;
           a.qf[idx] = (float)qn;
           if (i >= a.m_eq) {
-            const double yl = fmin(f * (a.ylh[idx] - yh), 0.0);
+            const double yl = f * (a.ylh[idx] - yh);
             a.ylh[idx] = yl;
             a.ylf[idx] = (float)yl;
           }
@@ -799,8 +801,13 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
         a.xst[idx] = xs;
         if (refine) {
           const double cn = f * (a.ch[idx] - kz);
-          const double ln = fmin(f * (a.lh[idx] - xh), 0.0);
-          const double un = fmax(f * (a.uh[idx] - xh), 0.0);
+          // exact in FP64: the candidate may sit a rounding outside its bounds
+          // (the FP32 iterate was projected onto FP32-rounded bounds, e.g. a
+          // fixed variable); the new round corrects that, so no clamping here.
+          // The round starts at x^ = y^ = 0 even if that is a rounding
+          // outside [l^, u^]: the first projected step restores feasibility.
+          const double ln = f * (a.lh[idx] - xh);
+          const double un = f * (a.uh[idx] - xh);
           a.ch[idx] = cn;
           a.lh[idx] = ln;
           a.uh[idx] = un;

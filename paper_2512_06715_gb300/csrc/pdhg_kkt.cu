@@ -269,7 +269,10 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
       to_avg = best;
     }
     if (restart) {
-      const double Dx = sqrt(dxa[to_avg]), Dy = sqrt(dya[to_avg]);
+      // distances since the last restart, back in round-0 units: a correction
+      // round's coordinates are Delta/Delta_0 times larger, and the
+      // "distance too small to update omega" test must not loosen with them
+      const double Dx = sqrt(dxa[to_avg]) * st->gap_w, Dy = sqrt(dya[to_avg]) * st->gap_w;
       double om = omega;
       if (Dx > 1e-10 && Dy > 1e-10) {
         const double th = st->omega_smooth;
