@@ -185,6 +185,17 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- our arm
+def max_over_ranks(value: float, device) -> float:
+    """The slowest rank's value (replicas: the job ends when the last one does)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def node_throughput(args, dev, stream, pdhg):
     """64 node LPs of one shared K (seeded commitment fixings) advanced by the
     same number of attempts, batched in one pdhg_solve_batched call and as one
@@ -291,11 +302,7 @@ def run_ours(args):
     d64, a64 = algorithmic_bytes(n, m, nnz, 8)
     att32 = r_mixed["iterations"]
     att64 = r64["iterations"]
-    sec_per_step = t_mixed / args.steps
-    if world > 1:
-        t = torch.tensor([sec_per_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec_per_step = float(t.item())
+    sec_per_step = max_over_ranks(t_mixed / args.steps, dev)
     value = world * att32 * (d32 + a32) / sec_per_step / 1e9
     fp64_gbs = att64 * (d64 + a64) / (t64 / max(1, args.steps // 2)) / 1e9
 
