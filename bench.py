@@ -136,11 +136,12 @@ def dram_traffic_record(kernel_src: Path, kernel: str):
     rec = ROOT / "profiles" / "dram_traffic.json"
     if not rec.exists():
         return None
-    d = json.loads(rec.read_text())
     h = hashlib.sha256(kernel_src.read_bytes()).hexdigest()[:16]
-    if d.get("kernel_source_sha256_16") != h or d.get("kernel") != kernel:
-        return None
-    return d
+    recs = json.loads(rec.read_text())
+    for d in recs if isinstance(recs, list) else [recs]:
+        if isinstance(d, dict) and d.get("kernel_source_sha256_16") == h and d.get("kernel") == kernel:
+            return d
+    return None
 
 
 # --------------------------------------------------------------------------- CPU oracle leg

@@ -71,3 +71,24 @@ def test_max_over_ranks_gloo():
         assert p.exitcode == 0
     got = dict(q.get(timeout=10) for _ in range(2))
     assert got == {0: 2.5, 1: 2.5}
+
+
+def test_dram_traffic_record_matches_kernel_and_source(tmp_path, monkeypatch):
+    """The committed traffic figure is used only for the same kernel variant and an
+    unchanged kernel source; the record file may hold one record or a list."""
+    import hashlib
+    sys.path.insert(0, str(ROOT))
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", tmp_path)
+    rec = {"kernel": "k_dual<float, 1>", "bytes_per_launch": 1.0, "kernel_source_sha256_16": h}
+    for content in (rec, [rec, {**rec, "kernel": "k_dual_pipe<float>", "bytes_per_launch": 2.0}]):
+        (prof / "dram_traffic.json").write_text(json.dumps(content))
+        assert bench.dram_traffic_record(src, "k_dual<float, 1>")["bytes_per_launch"] == 1.0
+        assert bench.dram_traffic_record(src, "k_dual<float, 4>") is None
+    src.write_text("changed")
+    assert bench.dram_traffic_record(src, "k_dual<float, 1>") is None
