@@ -92,14 +92,16 @@ typedef struct pdhg_opts {
   double step_growth_exp;    /* ... (1+(k+1)^-0.6) eta) (0.6)                         */
   int32_t ruiz_iters;       /* Ruiz l_inf passes (10)                                 */
   int32_t pock_chambolle;   /* 1: one Pock-Chambolle alpha=1 pass (1)                 */
-  double ir_reduction;      /* mixed: a refinement round ends at the first restart
-                               whose candidate has rel_kkt <= ir_reduction x that of
-                               the round's starting point (or <= tol); the candidate
-                               is folded into x*, y* in FP64 (0.5)                    */
-  double ir_force_reduction; /* mixed: a check whose better candidate is at or below
-                               this factor x the round start's rel_kkt restarts there
-                               (ending the round) even if the restart rule would not
-                               (0.1; <= ir_reduction)                                  */
+  double ir_reduction;      /* mixed: a refinement round ends at a check (without a
+                               restart) whose current iterate has rel_kkt <=
+                               ir_reduction x that of the round's start; pdhg_solve
+                               folds the iterate into x*, y* in FP64 and continues
+                               the same iteration in rescaled coordinates; the batched
+                               solver ends rounds at restarts instead (0.5)           */
+  double ir_force_reduction; /* batched, mixed: a check whose better candidate is at
+                               or below this factor x the round start's rel_kkt
+                               restarts there, ending the round, even if the restart
+                               rule would not (0.1; <= ir_reduction)                  */
   int32_t ir_max_rounds;    /* mixed: refinement rounds after the first (100000)      */
   int32_t trace;            /* 1: record per-attempt/per-check trace (testing) (0)    */
   double fixed_eta;         /* > 0: constant steps eta/omega, no restarts (0)         */

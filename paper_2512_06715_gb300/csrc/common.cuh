@@ -56,7 +56,7 @@ struct DevState {
   int32_t best_is_avg, numeric;
   double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
   // targets and limits
-  double tol, round_target, ir_red, round_force, ir_force;
+  double tol, round_target, ir_red;
   int64_t max_k, max_checks;
   uint64_t t_start, t_limit_ns;
   double t_tol[3];
@@ -68,9 +68,10 @@ struct DevState {
   int32_t art_total; // artificial restart against attempts of all rounds
   int32_t trace_on;
   int64_t trace_cap_a, trace_cap_c, n_trace_a, n_trace_c;
-  // refinement rounds (mixed mode): a restart whose candidate meets
-  // round_target ends the round instead of moving the iterate
-  int32_t refine;
+  // refinement rounds (mixed mode): a check whose current iterate meets
+  // round_target ends the round; fold = 1 asks the host to fold that iterate
+  // into x*, y* and continue the iteration in the new coordinates
+  int32_t refine, fold;
   // norms of the unscaled data and refinement scalars
   double qnorm, cnorm;
   double inv_dp, inv_dd;      // 1/Delta_P, 1/Delta_D

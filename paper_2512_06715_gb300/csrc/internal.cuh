@@ -50,7 +50,7 @@ struct RoundInit {
   double eta, omega;       // used when reset_steps
   int32_t reset_steps;     // 1: take eta/omega from the values above
   int32_t first_round;     // 1: restart the clock and the tolerance stamps
-  double tol, ir_red, ir_force;
+  double tol, ir_red;
   int64_t max_k, max_checks, k_offset;
   uint64_t t_limit_ns;
   double inv_dp, inv_dd;
@@ -59,6 +59,16 @@ struct RoundInit {
   int64_t trace_cap_a, trace_cap_c;
   int32_t refine;  // 1: refinement rounds (mixed precision)
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
+};
+
+// Device-state update of a refinement fold that continues the iteration in
+// new coordinates (Delta' = f Delta): scalings, restart-metric scale, the next
+// round's target, attempt bookkeeping.
+struct RoundContinue {
+  double f;              // Delta' / Delta
+  double inv_dp, inv_dd, gap_w;
+  double rel;            // rel-KKT of the folded point
+  int64_t max_k, max_checks, k_offset;
 };
 
 // Launch configuration of the two per-attempt kernels of one precision:
@@ -140,6 +150,10 @@ void launch_check(const IterArgs<T>& a, int grid_k, int grid_kt, int init, cudaS
 template <class T>
 void launch_accumulate(const IterArgs<T>& a, double* x_star, double* y_star, int grid,
                        cudaStream_t s);
+template <class T>
+void launch_recenter(const IterArgs<T>& a, double f, cudaStream_t s);
+void launch_state_continue(DevState* st, const RoundContinue& rc, const double* scalars,
+                           cudaStream_t s);
 void launch_ir_build(Workspace* w, double dp, double dd, bool make_f32, cudaStream_t s);
 void launch_output(Workspace* w, double* x_out, double* y_out, cudaStream_t s);
 

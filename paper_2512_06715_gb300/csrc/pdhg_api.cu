@@ -339,9 +339,10 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
   const bool fixed = o.fixed_eta > 0.0;
   int64_t k_done = 0, accepted = 0, restarts = 0, checks = 0;
   // kernels launched by this call: preparation (8 + 4 per rescaling pass),
-  // FP32 copies, then per round: correction build 4, state 1, init vectors 2,
-  // first primal step 1, initial check 3, one 64-attempt body (2 per attempt +
-  // a 4-kernel check) per executed check, accumulate 1; output 1.
+  // FP32 copies, then per round: correction build 4; for the first round state
+  // 1, init vectors 2, first primal step 1, initial check 3, for a continued
+  // round re-centering 1 and state 1; one 64-attempt body (2 per attempt + a
+  // 4-kernel check) per executed check, accumulate 1; output 1.
   const int passes = o.ruiz_iters + (o.pock_chambolle ? 1 : 0);
   int64_t launches = 8 + 4 * passes + (mixed ? 2 : 0) + 1;
   // Bound/objective rescaling is round 0 of the refinement form: the solver
@@ -360,46 +361,64 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
   int status = 0;
   int rounds = 0;
   IterArgs<T> a = make_args<T>(w);
+  bool fold = false;  // the previous round ended in a refinement fold
+  double fold_f = 1.0, fold_rel = 1.0;
   for (int r = 0; r < max_rounds; ++r) {
     launch_ir_build(w, dp, dd, mixed, s);
-    RoundInit ri{};
-    ri.reset_steps = (r == 0);
-    ri.eta = fixed ? o.fixed_eta : 0.0;
-    ri.omega = fixed ? o.fixed_omega : omega0;
-    ri.art_total = o.artificial_total ? 1 : 0;
-    ri.first_round = (r == 0);
-    ri.tol = o.tol;
-    ri.ir_red = o.ir_reduction;
-    ri.ir_force = o.ir_force_reduction;
-    ri.max_k = o.max_iters - k_done;
-    ri.max_checks = (ri.max_k + kCheckEvery - 1) / kCheckEvery + 1;
-    ri.k_offset = k_done;
-    ri.t_limit_ns = (uint64_t)(o.time_limit_s * 1e9);
-    ri.inv_dp = 1.0 / dp;
-    ri.inv_dd = 1.0 / dd;
-    ri.gap_w = dp0 / dp;
-    ri.fixed = fixed ? 1 : 0;
-    ri.trace_on = o.trace ? 1 : 0;
-    ri.trace_cap_a = w->trace_cap_a;
-    ri.trace_cap_c = w->trace_cap_c;
-    ri.refine = mixed ? 1 : 0;
-    ri.beta_suff = o.beta_sufficient;
-    ri.beta_nec = o.beta_necessary;
-    ri.beta_art = o.beta_artificial;
-    ri.omega_smooth = o.omega_smoothing;
-    ri.red_exp = o.step_reduction_exp;
-    ri.grow_exp = o.step_growth_exp;
-    if (r == 0 && !w->tune[mixed ? 1 : 0].done) {
+    if (fold) {
+      // continue the iteration in the new coordinates (see k_recenter)
+      launch_recenter<T>(a, fold_f, s);
+      RoundContinue cont{};
+      cont.f = fold_f;
+      cont.inv_dp = 1.0 / dp;
+      cont.inv_dd = 1.0 / dd;
+      cont.gap_w = dp0 / dp;
+      cont.rel = fold_rel;
+      cont.max_k = o.max_iters - k_done;
+      cont.max_checks = (cont.max_k + kCheckEvery - 1) / kCheckEvery + 1;
+      cont.k_offset = k_done;
+      launch_state_continue(w->st, cont, w->scalars, s);
+      launches += 4 + 2;
+    } else {
+      RoundInit ri{};
+      ri.reset_steps = (r == 0);
+      ri.eta = fixed ? o.fixed_eta : 0.0;
+      ri.omega = fixed ? o.fixed_omega : omega0;
+      ri.art_total = o.artificial_total ? 1 : 0;
+      ri.first_round = (r == 0);
+      ri.tol = o.tol;
+      ri.ir_red = o.ir_reduction;
+      ri.max_k = o.max_iters - k_done;
+      ri.max_checks = (ri.max_k + kCheckEvery - 1) / kCheckEvery + 1;
+      ri.k_offset = k_done;
+      ri.t_limit_ns = (uint64_t)(o.time_limit_s * 1e9);
+      ri.inv_dp = 1.0 / dp;
+      ri.inv_dd = 1.0 / dd;
+      ri.gap_w = dp0 / dp;
+      ri.fixed = fixed ? 1 : 0;
+      ri.trace_on = o.trace ? 1 : 0;
+      ri.trace_cap_a = w->trace_cap_a;
+      ri.trace_cap_c = w->trace_cap_c;
+      ri.refine = mixed ? 1 : 0;
+      ri.beta_suff = o.beta_sufficient;
+      ri.beta_nec = o.beta_necessary;
+      ri.beta_art = o.beta_artificial;
+      ri.omega_smooth = o.omega_smoothing;
+      ri.red_exp = o.step_reduction_exp;
+      ri.grow_exp = o.step_growth_exp;
+      if (r == 0 && !w->tune[mixed ? 1 : 0].done) {
+        launch_state_init(w->st, ri, w->scalars, s);
+        launch_init_iterates<T>(a, 0, s);
+        launch_adjoint<T>(a, w->grid_kt, s, 1);
+        if ((rc = autotune<T>(w, a, s)) != PDHG_OK) return rc;
+      }
+      if (!o.host_loop && (rc = build_graph<T>(w)) != PDHG_OK) return rc;
       launch_state_init(w->st, ri, w->scalars, s);
       launch_init_iterates<T>(a, 0, s);
-      launch_adjoint<T>(a, w->grid_kt, s, 1);
-      if ((rc = autotune<T>(w, a, s)) != PDHG_OK) return rc;
+      run_adjoint<T>(w, a, s);
+      launch_check<T>(a, w->grid_k, w->grid_kt, 1, s);
+      launches += 4 + 1 + 2 + 1 + 3;
     }
-    if (!o.host_loop && (rc = build_graph<T>(w)) != PDHG_OK) return rc;
-    launch_state_init(w->st, ri, w->scalars, s);
-    launch_init_iterates<T>(a, 0, s);
-    run_adjoint<T>(w, a, s);
-    launch_check<T>(a, w->grid_k, w->grid_kt, 1, s);
     if (o.host_loop) {
       // Same kernels as the graph body, launched from the host; the done flag
       // is read after every check (one host wait per 64 attempts).
@@ -425,17 +444,18 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     accepted += h.accepted;
     restarts += h.restarts;
     checks += h.checks;
-    launches += 4 + 1 + 2 + 1 + 3 + h.checks * (2 * kCheckEvery + 4) + 1;
+    launches += h.checks * (2 * kCheckEvery + 4) + 1;
     rounds = r;
     status = h.status;
     if (h.status != 0) break;  // optimal or a limit
-    // the round ended at a restart that met its target: refine from that
-    // candidate (the device sets the next round's target at its first check)
-    const double rel = std::max(h.rel_kkt, 1e-300);
+    // Refinement fold: the round's current iterate is now part of x*, y*.
     // Delta_P / Delta_D grow by 1/rel_kkt relative to round 0, so their ratio
     // (and with it the meaning of the primal weight) stays the same.
-    double scale = 1.0 / rel;
-    scale = std::min(scale, 1e12);
+    const double rel = std::max(h.rel_kkt, 1e-300);
+    const double scale = std::min(1.0 / rel, 1e12);
+    fold = true;
+    fold_f = dp0 * scale / dp;
+    fold_rel = rel;
     dp = dp0 * scale;
     dd = dd0 * scale;
     if (r + 1 == max_rounds) status = PDHG_STATUS_ITER_LIMIT;

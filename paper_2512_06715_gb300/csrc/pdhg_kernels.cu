@@ -591,8 +591,7 @@ __global__ void k_state_init(DevState* st, RoundInit r, const double* scalars) {
   st->numeric = 0;
   st->tol = r.tol;
   st->ir_red = r.ir_red;
-  st->ir_force = r.ir_force;
-  st->round_force = 0.0;
+  st->fold = 0;
   st->round_target = r.tol;
   st->max_k = r.max_k;
   st->max_checks = r.max_checks;

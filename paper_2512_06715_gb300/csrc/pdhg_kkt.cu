@@ -202,7 +202,6 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     // a refinement round ends at a restart whose candidate improves on the
     // round's starting point by the factor ir_red
     st->round_target = st->refine ? fmax(st->tol, st->ir_red * rel[0]) : st->tol;
-    st->round_force = st->refine ? fmax(st->tol, st->ir_force * rel[0]) : 0.0;
     st->rel_p = relp[0];
     st->rel_d = reld[0];
     st->rel_gap = relg[0];
@@ -261,13 +260,6 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
               ((double)st->since_restart >=
                st->beta_art * (double)(st->art_total ? st->k_offset + st->k : st->k));
     st->kkt_prev = kc;
-    if (st->refine && !restart && rel[best] <= st->round_force) {
-      // the round's error fell far below its start without a restart: restart
-      // at the better candidate so that the round can end there (the FP32
-      // correction would otherwise approach its own rounding floor)
-      restart = 1;
-      to_avg = best;
-    }
     if (restart) {
       // distances since the last restart, back in round-0 units: a correction
       // round's coordinates are Delta/Delta_0 times larger, and the
@@ -282,26 +274,27 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
       st->kkt0 = sqrt(om * rp2s[to_avg] + rd2s[to_avg] / om + gh[to_avg] * gh[to_avg]);
       st->kkt_prev = st->kkt0;
       st->restarts += 1;
-      if (st->refine && rel[to_avg] <= st->round_target) {
-        // Refinement: this restart ends the round.  Its candidate joins x*, y*
-        // in FP64 and the next round restarts from it at x^ = y^ = 0 with the
-        // same eta and omega, which is the same restart in new coordinates.
-        done = 1;
-        status = 0;
-        restart = 0;
-        st->best_is_avg = to_avg;
-        st->rel_p = relp[to_avg];
-        st->rel_d = reld[to_avg];
-        st->rel_gap = relg[to_avg];
-        st->rel_kkt = rel[to_avg];
-        st->pobj = P[to_avg];
-        st->dobj = D[to_avg];
-      } else {
-        st->avg_div = st->wsum;
-        st->wsum = 0.0;
-        st->since_restart = 0;
-      }
+      st->avg_div = st->wsum;
+      st->wsum = 0.0;
+      st->since_restart = 0;
     }
+  }
+  if (st->refine && !done && !restart && !st->fixed && rel[0] <= st->round_target) {
+    // Refinement: the current iterate joins x*, y* in FP64 and the round ends;
+    // the host re-expresses the whole iteration state (iterate, pending step,
+    // averages, restart anchors) in the new coordinates (k_recenter), so the
+    // method continues exactly where it was, with the FP32 values now
+    // corrections of a smaller error.
+    done = 1;
+    status = 0;
+    st->fold = 1;
+    st->best_is_avg = 0;
+    st->rel_p = relp[0];
+    st->rel_d = reld[0];
+    st->rel_gap = relg[0];
+    st->rel_kkt = rel[0];
+    st->pobj = P[0];
+    st->dobj = D[0];
   }
   st->restart_now = restart;
   st->restart_to_avg = to_avg;
@@ -391,6 +384,80 @@ __global__ void k_accumulate(IterArgs<T> a, double* x_star, double* y_star) {
       y_star[t] = y_star[t] + yv * inv_dd;
     }
   }
+}
+
+// Refinement fold (mixed precision), after x* += x^_c / Delta and the new
+// correction data for Delta' = f Delta: every FP32 vector of the iteration is
+// re-expressed in the new coordinates v' = f (v - x^_c) (sums of eta-weighted
+// iterates: f (sum - wsum x^_c)).  The iterate becomes 0, so K^T y^ = 0; the
+// restart anchors and the averages move with it; the pending primal step is
+// recomputed from the new data, which in exact arithmetic is the same step.
+// Step size, primal weight, average weights and restart window are untouched,
+// so the iteration continues where it was.
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_recenter(IterArgs<T> a, double f) {
+  DevState* st = a.st;
+  const int p = st->par;
+  const double wsum = st->wsum;
+  const T tau = (T)(st->eta / st->omega);
+  T* x = a.x[p];
+  T* y = a.y[p];
+  double acc[1] = {0.0};
+  const int64_t N = a.n > a.m ? a.n : a.m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < a.m) {
+      const double yc = (double)y[t];
+      a.ya[t] = (T)(f * ((double)a.ya[t] - yc));
+      a.ybar[t] = (T)(f * ((double)a.ybar[t] - wsum * yc));
+      y[t] = 0;
+    }
+    if (t < a.n) {
+      const double xc = (double)x[t];
+      a.xa[t] = (T)(f * ((double)a.xa[t] - xc));
+      a.xbar[t] = (T)(f * ((double)a.xbar[t] - wsum * xc));
+      x[t] = 0;
+      a.KTy[p][t] = 0;
+      T v = -tau * a.c[t];
+      v = min(max(v, a.l[t]), a.u[t]);
+      a.x[1 - p][t] = v;
+      acc[0] += (double)v * (double)v;
+    }
+  }
+  if (publish_partials<1>(acc, a.partials, &st->counter)) {
+    double tot[1];
+    final_sum<1>(a.partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      st->dx2 = tot[0];
+      st->counter = 0;
+    }
+  }
+}
+
+__global__ void k_state_continue(DevState* st, RoundContinue rc, const double* scalars) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->inv_dp = rc.inv_dp;
+  st->inv_dd = rc.inv_dd;
+  st->gap_w = rc.gap_w;
+  st->const_p = scalars[6];
+  st->const_d = scalars[7];
+  // KKT_w with the gap weighted back to round-0 units scales by f as a whole
+  st->kkt0 *= rc.f;
+  st->kkt_prev *= rc.f;
+  st->round_target = fmax(st->tol, st->ir_red * rc.rel);
+  st->k_offset = rc.k_offset;
+  st->k = 0;
+  st->max_k = rc.max_k;
+  st->max_checks = rc.max_checks;
+  st->accepted = 0;
+  st->restarts = 0;
+  st->checks = 0;
+  st->restart_now = 0;
+  st->done = 0;
+  st->status = 0;
+  st->fold = 0;
+  st->counter = 0;
+  st->counter2 = 0;
 }
 
 // Correction LP of a refinement round (Gleixner, Steffy and Wolter's
@@ -487,6 +554,16 @@ void launch_accumulate(const IterArgs<T>& a, double* x_star, double* y_star, int
   k_accumulate<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a, x_star, y_star);
 }
 
+template <class T>
+void launch_recenter(const IterArgs<T>& a, double f, cudaStream_t s) {
+  k_recenter<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a, f);
+}
+
+void launch_state_continue(DevState* st, const RoundContinue& rc, const double* scalars,
+                           cudaStream_t s) {
+  k_state_continue<<<1, 32, 0, s>>>(st, rc, scalars);
+}
+
 void launch_ir_build(Workspace* w, double dp, double dd, bool make_f32, cudaStream_t s) {
   launch_spmv64(w->K.v64(), w->x_star, w->scr_m, w->grid_k, s);
   launch_spmv64(w->KT.v64(), w->y_star, w->scr_n, w->grid_kt, s);
@@ -510,5 +587,7 @@ template void launch_check<float>(const IterArgs<float>&, int, int, int, cudaStr
 template void launch_accumulate<double>(const IterArgs<double>&, double*, double*, int,
                                         cudaStream_t);
 template void launch_accumulate<float>(const IterArgs<float>&, double*, double*, int, cudaStream_t);
+template void launch_recenter<double>(const IterArgs<double>&, double, cudaStream_t);
+template void launch_recenter<float>(const IterArgs<float>&, double, cudaStream_t);
 
 }  // namespace ucpdhg

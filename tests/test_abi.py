@@ -19,6 +19,8 @@ def lib():
 
 def _declared(header: str) -> list[str]:
     text = (ROOT / "include" / header).read_text()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # comments are not declarations
+    text = re.sub(r"//[^\n]*", " ", text)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:\w+\s+)+\**\s*(\w+)\s*\(", text, re.M)))
 
 
