@@ -96,12 +96,7 @@ typedef struct pdhg_opts {
                                restart) whose current iterate has rel_kkt <=
                                ir_reduction x that of the round's start; pdhg_solve
                                folds the iterate into x*, y* in FP64 and continues
-                               the same iteration in rescaled coordinates; the batched
-                               solver ends rounds at restarts instead (0.5)           */
-  double ir_force_reduction; /* batched, mixed: a check whose better candidate is at
-                               or below this factor x the round start's rel_kkt
-                               restarts there, ending the round, even if the restart
-                               rule would not (0.1; <= ir_reduction)                  */
+                               the same iteration in rescaled coordinates (0.5)      */
   int32_t ir_max_rounds;    /* mixed: refinement rounds after the first (100000)      */
   int32_t trace;            /* 1: record per-attempt/per-check trace (testing) (0)    */
   double fixed_eta;         /* > 0: constant steps eta/omega, no restarts (0)         */

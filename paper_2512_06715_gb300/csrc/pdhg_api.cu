@@ -153,8 +153,9 @@ static void run_adjoint(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
 
 // Picks, by timing on this workspace's matrix, the variant (1, 2 or 4 slices
 // a warp sweeps together, or 0: the software-pipelined single-slice form) and
-// the grid size (2 to 8 blocks per SM) of each per-attempt kernel.  The candidate launches run real attempts on scratch state; the
-// caller re-initialises the iterates afterwards.
+// the grid size (2 to 8 blocks per SM) of each per-attempt kernel.  The
+// candidate launches run real attempts on scratch state; the caller
+// re-initialises the iterates afterwards.
 template <class T>
 static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   const int pi = sizeof(T) == 8 ? 0 : 1;
@@ -277,8 +278,7 @@ static int validate_opts(const pdhg_opts* o) {
     return fail(PDHG_ERR_UNSUPPORTED, "opts: check_every must be 64");
   if (o->ruiz_iters < 0 || o->ruiz_iters > 100)
     return fail(PDHG_ERR_INVALID_ARG, "opts: ruiz_iters out of range");
-  if (o->ir_max_rounds < 0 || !(o->ir_reduction > 0.0) || !(o->ir_reduction < 1.0) ||
-      !(o->ir_force_reduction > 0.0) || !(o->ir_force_reduction <= o->ir_reduction))
+  if (o->ir_max_rounds < 0 || !(o->ir_reduction > 0.0) || !(o->ir_reduction < 1.0))
     return fail(PDHG_ERR_INVALID_ARG, "opts: refinement settings out of range");
   if (o->fixed_eta < 0.0 || (o->fixed_eta > 0.0 && !(o->fixed_omega > 0.0)))
     return fail(PDHG_ERR_INVALID_ARG, "opts: fixed_eta needs fixed_omega > 0");
@@ -516,7 +516,6 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->ruiz_iters = 10;
   o->pock_chambolle = 1;
   o->ir_reduction = 0.5;
-  o->ir_force_reduction = 0.1;
   o->ir_max_rounds = 100000;
   o->trace = 0;
   o->fixed_eta = 0.0;

@@ -9,14 +9,16 @@
 // row, its lanes own instances, the row's column/value loads are broadcasts
 // and the gather x[col * BP + b] is one contiguous 128/256 B access.
 //
-// Refinement rounds run inside the graph: when an instance's round ends at a
-// check, the next correction LP follows elementwise from the FP64 products the
-// check already computed (K x^ and K^T y^ of the chosen candidate):
+// Refinement rounds run inside the graph: when an instance's current iterate
+// (x^, y^) halves the round's starting rel-KKT at a check without a restart,
+// the next correction LP follows elementwise from the FP64 products the check
+// already computed (K x^ and K^T y^):
 //   q^' = f (q^ - K x^),  c^' = f (c^ - K^T y^),  [l^',u^'] = f ([l^,u^] - x^),
 //   y_lo^' = f (y_lo^ - y^),  f = Delta'/Delta,  x* += x^/Delta,  y* += y^/Delta
-// and the instance restarts from x^ = 0, y^ = 0 (K x^ = K^T y^ = 0).  The
-// whole batch is one CUDA graph whose while loop runs until every instance is
-// done.
+// and the iteration state moves to the new coordinates v' = f (v - x^): the
+// iterate becomes 0 (K x^ = K^T y^ = 0), anchors and averages shift with it,
+// step size, primal weight and restart window carry over.  The whole batch is
+// one CUDA graph whose while loop runs until every instance is done.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -45,7 +47,7 @@ struct BInst {
   int32_t done, status, rounds, act;  // act: takes part in the next attempts
   int32_t refine, finalize, cand_avg, pad;
   double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
-  double round_target, round_force;
+  double round_target;
   double dp, dd;          // Delta_P, Delta_D of the current round
   double next_scale;      // Delta' / Delta for the refinement step
   double const_p, const_d;
@@ -55,7 +57,7 @@ struct BInst {
 };
 
 struct BGlobal {
-  double tol, red, force;
+  double tol, red;
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
   int64_t max_k;
   uint64_t t_start, t_limit_ns;
@@ -627,7 +629,6 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
       if (init) {
         I.kkt0 = I.kkt_prev = kw[0];
         I.round_target = fmax(g->tol, g->red * rel[0]);
-        I.round_force = fmax(g->tol, g->force * rel[0]);
       } else {
         I.checks += 1;
         I.pending_w = 0.0;
@@ -670,10 +671,6 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
                         (kc <= g->beta_nec * I.kkt0 && kc > I.kkt_prev) ||
                         ((double)I.since_restart >= g->beta_art * (double)I.k_total);
           I.kkt_prev = kc;
-          if (!restart && rel[best] <= I.round_force) {
-            restart = 1;  // forced: the round ends at the better candidate
-            to_avg = best;
-          }
           if (restart) {
             // distances in round-0 units (the correction coordinates are Delta
             // times larger): the "too small to update omega" test stays fixed
@@ -684,36 +681,35 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
             I.omega = om;
             const double k0 = sqrt(om * rp2s[to_avg] + rd2s[to_avg] / om + gh[to_avg] * gh[to_avg]);
             I.restarts += 1;
-            if (rel[to_avg] <= I.round_target) {
-              // refinement: this restart ends the round; its candidate joins
-              // x*, y* and the next round restarts from it at x^ = y^ = 0
-              const double relb = fmax(rel[to_avg], 1e-300);
-              const double scale = fmin(1.0 / relb, 1e12);
-              I.refine = 1;
-              I.cand_avg = to_avg;
-              const double f = scale / I.dp;  // Delta_P = Delta_D here
-              I.next_scale = f;
-              I.round_target = fmax(g->tol, g->red * relb);
-              I.round_force = fmax(g->tol, g->force * relb);
-              I.rounds += 1;
-              // the candidate's KKT_w in the new scaling: every term scales by f
-              I.kkt0 = f * k0;
-              I.kkt_prev = I.kkt0;
-              I.rel_p = relp[to_avg];
-              I.rel_d = reld[to_avg];
-              I.rel_gap = relg[to_avg];
-              I.rel_kkt = rel[to_avg];
-              I.pobj = P[to_avg];
-              I.dobj = D[to_avg];
-            } else {
-              I.kkt0 = k0;
-              I.kkt_prev = k0;
-              I.avg_div = I.wsum;
-              I.wsum = 0.0;
-              I.since_restart = 0;
-              I.restart_now = 1;
-              I.restart_to_avg = to_avg;
-            }
+            I.kkt0 = k0;
+            I.kkt_prev = k0;
+            I.avg_div = I.wsum;
+            I.wsum = 0.0;
+            I.since_restart = 0;
+            I.restart_now = 1;
+            I.restart_to_avg = to_avg;
+          } else if (rel[0] <= I.round_target) {
+            // refinement fold (as pdhg_solve): the current iterate joins x*, y*
+            // and kb_apply re-expresses the iteration state in the new
+            // coordinates; step size, primal weight, averages and restart
+            // window carry over
+            const double relb = fmax(rel[0], 1e-300);
+            const double scale = fmin(1.0 / relb, 1e12);
+            const double f = scale / I.dp;  // Delta_P = Delta_D here
+            I.refine = 1;
+            I.cand_avg = 0;
+            I.next_scale = f;
+            I.round_target = fmax(g->tol, g->red * relb);
+            I.rounds += 1;
+            // KKT_w with the gap weighted back to round-0 units scales by f
+            I.kkt0 *= f;
+            I.kkt_prev *= f;
+            I.rel_p = relp[0];
+            I.rel_d = reld[0];
+            I.rel_gap = relg[0];
+            I.rel_kkt = rel[0];
+            I.pobj = P[0];
+            I.dobj = D[0];
           }
         }
       }
@@ -742,6 +738,7 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
   const double f = I.next_scale;
   const double idp = 1.0 / I.dp, idd = 1.0 / I.dd;
   const double iw = I.wsum > 0.0 ? 1.0 / I.wsum : 0.0;
+  const double wsum = I.wsum;
   const double div = I.avg_div;
   const int cand_avg = I.cand_avg;
   const float tau = (float)(I.eta / I.omega);
@@ -763,6 +760,8 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
         const double ys = a.yst[idx] + yh * idd;
         a.yst[idx] = ys;
         if (refine) {
+          // fold at the current iterate (cand_avg = 0): new correction data,
+          // then the state in the new coordinates v' = f (v - y^c)
           const double qn = f * (a.qh[idx] - kz);
           a.qh[idx] = qn;
           a.qf[idx] = (float)qn;
@@ -771,9 +770,10 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
             a.ylh[idx] = yl;
             a.ylf[idx] = (float)yl;
           }
-          a.y[0][idx] = a.y[1][idx] = 0.f;
-          a.Kx[0][idx] = a.Kx[1][idx] = 0.f;
-          a.ybar[idx] = a.ya[idx] = 0.f;
+          a.ya[idx] = (float)(f * ((double)a.ya[idx] - yh));
+          a.ybar[idx] = (float)(f * ((double)a.ybar[idx] - wsum * yh));
+          a.y[p][idx] = 0.f;
+          a.Kx[p][idx] = 0.f;
         }
         scd += a.q_obj[i] * ys;
       }
@@ -814,11 +814,14 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
           a.cf[idx] = (float)cn;
           a.lf[idx] = (float)ln;
           a.uf[idx] = (float)un;
-          a.KTy[0][idx] = a.KTy[1][idx] = 0.f;
-          a.xbar[idx] = a.xa[idx] = 0.f;
-          a.x[0][idx] = 0.f;
-          float v = fminf(fmaxf(-tau * (float)cn, (float)ln), (float)un);
-          a.x[1][idx] = v;
+          a.xa[idx] = (float)(f * ((double)a.xa[idx] - xh));
+          a.xbar[idx] = (float)(f * ((double)a.xbar[idx] - wsum * xh));
+          a.KTy[p][idx] = 0.f;
+          a.x[p][idx] = 0.f;
+          // the pending primal step from the new data (the same step in exact
+          // arithmetic)
+          float v = fminf(fmaxf(-tau * a.cf[idx], a.lf[idx]), a.uf[idx]);
+          a.x[1 - p][idx] = v;
           sdx += (double)v * (double)v;
         }
         scp += a.c_obj[j] * xs;
@@ -856,16 +859,11 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
           J.const_d = s2;
         }
         if (J.refine) {
-          // fresh round of the correction LP from x^ = 0, y^ = 0
+          // the same iteration in the new coordinates: only the scale and the
+          // pending step's length change
           J.dx2 = s0;
           J.dp *= J.next_scale;
           J.dd = J.dp;
-          J.par = 1 - 1;  // current buffers are index 0 (x^ = 0); the candidate x'' is in 1
-          J.accepted_last = 0;
-          J.w_last = J.pending_w = J.wsum = 0.0;
-          J.k = 0;
-          J.since_restart = 0;
-          J.restart_now = 0;
         }
       }
       J.restart_now = 0;
@@ -1206,7 +1204,6 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   BGlobal gin{};
   gin.tol = o.tol;
   gin.red = o.ir_reduction;
-  gin.force = o.ir_force_reduction;
   gin.beta_suff = o.beta_sufficient;
   gin.beta_nec = o.beta_necessary;
   gin.beta_art = o.beta_artificial;

@@ -31,7 +31,7 @@ class pdhg_opts(C.Structure):
                 ("beta_artificial", C.c_double), ("omega_smoothing", C.c_double),
                 ("step_reduction_exp", C.c_double), ("step_growth_exp", C.c_double),
                 ("ruiz_iters", C.c_int32), ("pock_chambolle", C.c_int32),
-                ("ir_reduction", C.c_double), ("ir_force_reduction", C.c_double),
+                ("ir_reduction", C.c_double),
                 ("ir_max_rounds", C.c_int32), ("trace", C.c_int32),
                 ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
                 ("bound_obj_rescale", C.c_int32), ("artificial_total", C.c_int32),
