@@ -1,0 +1,74 @@
+"""Parity at the bench's full size (collected after the small-case parity tests):
+the 6717-bus, 96-period relaxation (n = 1.03 M, m = 3.08 M, nnz = 10.5 M) with
+the autotuned launch configuration the bench uses.
+
+- Constant-step attempts: 64 attempts on the GPU against the oracle's 64 attempts
+  on the same LP (the oracle finishes them in seconds at this size); FP64 to 1e-9
+  and FP32 to 1e-4 (a float32 emulation of the same 64 attempts on the CPU is
+  within 2e-6), relative to the largest entry.
+- The FP64 rel-KKT the GPU reports for its returned point, after a short adaptive
+  solve in mixed precision, equals the oracle's recomputation from that point (a
+  property of the check reductions that holds at any size)."""
+import numpy as np
+import pytest
+
+from oracle.lp import kkt
+from oracle.pdhg import pdhg_solve
+from oracle.scaling import rescale
+from tests.conftest import instance_lp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WORKLOAD = "uc6717_g1000_T96"
+
+
+@pytest.fixture(scope="module")
+def full():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_06715_gb300 import build
+    from paper_2512_06715_gb300.instances import workload
+    build.build()
+    inst = workload(WORKLOAD)
+    lp = instance_lp(inst)
+    slp, _, _ = rescale(lp)
+    # Pock-Chambolle rescaling with alpha = 1 bounds ||K~||_2 by 1, so constant
+    # steps eta = 0.9 keep the iteration stable: errors do not grow over the 64
+    # attempts and the comparison measures rounding, not amplification
+    eta = 0.9
+    omega = np.linalg.norm(slp.c) / np.linalg.norm(slp.q)
+    ref = pdhg_solve(lp, fixed=dict(eta=eta, omega=omega), stop_after=64)
+    return inst, lp, eta, omega, ref
+
+
+def _rel_err(x, y, ref):
+    cands = [(ref.x_cur, ref.y_cur), (ref.x_avg, ref.y_avg)]
+    return min(max(np.abs(x - a).max() / np.abs(a).max(), np.abs(y - b).max() / np.abs(b).max())
+               for a, b in cands)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_fixed_steps_full_size(full, precision, tol):
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst, lp, eta, omega, ref = full
+    ws = Workspace.from_instance(inst, default_opts(precision=precision, fixed_eta=eta, fixed_omega=omega,
+                                                    max_iters=64, tol=1e-30, time_limit_s=120.0))
+    x, y, r = ws.solve()
+    ws.close()
+    assert r["iterations"] == 64 and r["restarts"] == 0
+    err = _rel_err(x.cpu().numpy(), y.cpu().numpy(), ref)
+    assert err <= tol, err
+
+
+def test_reported_rel_kkt_full_size(full):
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst, lp, _, _, _ = full
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", max_iters=4096, tol=1e-8,
+                                                    time_limit_s=120.0))
+    x, y, r = ws.solve()
+    ws.close()
+    chk = kkt(lp, x.cpu().numpy(), y.cpu().numpy())
+    assert np.isfinite(chk.rel_kkt)
+    assert abs(chk.rel_kkt - r["rel_kkt"]) <= 1e-2 * r["rel_kkt"] + 1e-12, (chk.rel_kkt, r["rel_kkt"])
+    assert abs(chk.primal_obj - r["primal_obj"]) <= 1e-8 * max(1.0, abs(chk.primal_obj))
