@@ -30,7 +30,12 @@ import threading
 import time
 from pathlib import Path
 
-import numpy as np
+# The CPU oracle leg reports "cores": 1; keep NumPy's BLAS (vector norms) on one
+# thread so that the figure is what ran.  Set before NumPy loads its BLAS.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
