@@ -137,6 +137,10 @@ typedef struct pdhg_result {
   double eta, omega;           /* final step size and primal weight            */
   int64_t kernel_launches;     /* kernels this call ran (graph bodies counted
                                   once per executed body)                      */
+  int32_t returned_average;    /* 1: the last round's returned candidate was the
+                                  step-weighted average since the last restart,
+                                  0: the current iterate                       */
+  int32_t reserved;
 } pdhg_result;
 
 /* Fill *o with the defaults listed above. */
@@ -196,9 +200,11 @@ const char *pdhg_last_error(void);
  *     GPU loading the library holds until the process exits.  n > 2^21 is
  *     rejected with PDHG_ERR_UNSUPPORTED before any device work.
  *   - No cudaMalloc, cudaFree or allocating library call is made.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - The first call in a CUDA context (the device's primary context, or a
+ *     driver-API context the caller made current) looks up the array's device
+ *     address in that context (cudaGetSymbolAddress) and caches it by the
+ *     context's unique id, so a context created after cudaDeviceReset gets its
+ *     own lookup; make that first call before any stream capture.
  *   - Every call shares the array and finds the previous call's contents in
  *     it (it clears what must start at zero); calls that overlap on the GPU,
  *     in different streams or threads, race on it.
@@ -226,8 +232,9 @@ int pdhg_apply_K(void *ws, int32_t transpose, int32_t precision, const double *i
 
 /* Copy the trace of the last solve (opts.trace = 1) to host arrays:
  *   attempts [cap_a][5]: eta, omega, accepted, eta_max, eta_next
- *   checks   [cap_c][8]: attempts, restart, to_average, omega_after, KKT_w of the
- *                       current and average iterate, rel_kkt of the current and average
+ *   checks   [cap_c][12]: attempts, restart, to_average, omega_after, KKT_w of the
+ *                       current and average iterate, rel_kkt of the current and average,
+ *                       rel_p, rel_d, rel_gap of the current iterate, eta after the check
  * *n_a, *n_c receive the counts recorded (may exceed the caps). */
 int pdhg_get_trace(void *ws, double *attempts, int64_t cap_a, double *checks, int64_t cap_c,
                    int64_t *n_a, int64_t *n_c);

@@ -100,12 +100,14 @@ def kkt(lp: LP, x: np.ndarray, y: np.ndarray) -> KKT:
     rd = lam - lam_proj
     y_lo = lp.dual_lower()
     ineq = np.arange(lp.m) >= lp.m_eq
-    ylo_term = np.where(ineq & np.isfinite(y_lo), y_lo * np.minimum(slack, 0.0), 0.0)
+    # infinite bounds are masked before they multiply (no inf * 0 is formed)
+    ylo_fin = ineq & np.isfinite(y_lo)
+    ylo_term = np.where(ylo_fin, y_lo, 0.0) * np.where(ylo_fin, np.minimum(slack, 0.0), 0.0)
     P = float(lp.c @ x + ylo_term.sum())
     lf = np.isfinite(lp.l)
     uf = np.isfinite(lp.u)
-    bound = np.where(lf, lp.l * np.maximum(lam_proj, 0.0), 0.0).sum() - \
-        np.where(uf, lp.u * np.maximum(-lam_proj, 0.0), 0.0).sum()
+    bound = (np.where(lf, lp.l, 0.0) * np.where(lf, np.maximum(lam_proj, 0.0), 0.0)).sum() - \
+        (np.where(uf, lp.u, 0.0) * np.where(uf, np.maximum(-lam_proj, 0.0), 0.0)).sum()
     D = float(lp.q @ y + bound)
     rel_p = float(np.linalg.norm(rp) / (1.0 + np.linalg.norm(lp.q)))
     rel_d = float(np.linalg.norm(rd) / (1.0 + np.linalg.norm(lp.c)))

@@ -31,9 +31,17 @@ ones; its code shares nothing with this file):
   the iterate, anchor and KKT_0 move to the candidate (KKT_0 taken with the
   new omega, which also becomes the "previous" value) and the averages reset.
 
-``schedule`` replays a recorded run: per attempt (eta, omega, accepted) and per
-check (restart, to_average); the oracle then follows those decisions while still
-computing and returning its own, so that both can be compared.
+``schedule`` replays a recorded run: per attempt (eta, accepted) and per check
+(restart, to_average); the oracle then follows those decisions while still
+computing and returning its own, so that both can be compared.  The primal
+weight is never replayed: it is always the oracle's own, updated at each
+restart from the oracle's own iterates, so a replay compares the primal-weight
+update too.  (The step size is replayed because the GPU evaluates the factors
+(k+1)^-0.3 and (k+1)^-0.6 in FP32; the oracle's own eta_next is logged beside.)
+
+The three rules are separate functions (``step_size_update``,
+``restart_decision``, ``primal_weight_update``) so that each can be checked by
+hand on its own.
 """
 from __future__ import annotations
 
@@ -83,6 +91,39 @@ class PDHGResult:
     y_avg: np.ndarray | None = None
 
 
+def step_size_update(eta: float, omega: float, dx: np.ndarray, dy: np.ndarray, Kdx: np.ndarray, k: int,
+                     opts: PDLPOptions):
+    """Adaptive step rule of attempt k (1-based count of attempts so far) with
+    dx = x+ - x, dy = y+ - y, Kdx = K dx.  Returns (accept, eta_max, eta_next)."""
+    movement = omega * float(dx @ dx) + float(dy @ dy) / omega
+    interaction = 2.0 * abs(float(dy @ Kdx))
+    eta_max = movement / interaction if interaction > 0 else np.inf
+    eta_next = min((1.0 - (k + 1) ** (-opts.step_reduction_exp)) * eta_max,
+                   (1.0 + (k + 1) ** (-opts.step_growth_exp)) * eta)
+    return eta <= eta_max, eta_max, eta_next
+
+
+def restart_decision(kkt_cur: float, kkt_avg: float, has_avg: bool, kkt0: float, kkt_prev: float,
+                     since_restart: int, attempts: int, opts: PDLPOptions):
+    """Restart test at a check.  The candidate is the average when it has a
+    smaller KKT_omega than the current iterate.  Returns (restart, to_avg, kkt_cand)."""
+    to_avg = bool(has_avg and kkt_avg < kkt_cur)
+    kc = kkt_avg if to_avg else kkt_cur
+    restart = (kc <= opts.beta_sufficient * kkt0) or \
+              (kc <= opts.beta_necessary * kkt0 and kc > kkt_prev) or \
+              (since_restart >= opts.beta_artificial * attempts)
+    return bool(restart), to_avg, kc
+
+
+def primal_weight_update(omega: float, dist_x: float, dist_y: float, theta: float) -> float:
+    """Primal weight after a restart that moved the primal iterate by dist_x and
+    the dual by dist_y since the previous restart (log-space smoothing theta);
+    unchanged when either distance is below 1e-10."""
+    if dist_x > 1e-10 and dist_y > 1e-10:
+        return float(np.exp(theta * np.log(dist_y / dist_x) + (1.0 - theta) * np.log(omega)))
+    return omega
+
+
 def _kkt_omega(slp: LP, Dr, Dc, lp: LP, x_s, y_s, omega):
     """Scaled-space restart metric and unscaled rel-KKT of one candidate."""
     res = kkt(lp, Dc * x_s, Dr * y_s)
@@ -100,7 +141,7 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
 
     fixed      -- dict(eta=..., omega=...): constant steps, every attempt accepted, no
                   restarts; runs exactly ``stop_after`` attempts.
-    schedule   -- dict(attempts=[(eta, omega, accepted), ...], checks=[(restart, to_avg), ...])
+    schedule   -- dict(attempts=[(eta, accepted), ...], checks=[(restart, to_avg), ...])
     stop_after -- stop after this many attempts (status "stopped").
     start      -- (x, y) of the ORIGINAL LP to start from instead of the projection of 0.
     """
@@ -147,23 +188,18 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
             if k >= max_attempts or (stop_after is not None and k >= stop_after):
                 break
             if sched_a is not None:
-                eta, omega = float(sched_a[k][0]), float(sched_a[k][1])
+                eta = float(sched_a[k][0])
             tau, sigma = eta / omega, eta * omega
             xn = np.clip(x - tau * (c - KTy), l, u)
             Kxn = K @ xn
             yn = np.maximum(y + sigma * (q - 2.0 * Kxn + Kx), y_lo)
-            dx, dy = xn - x, yn - y
-            movement = omega * (dx @ dx) + (dy @ dy) / omega
-            interaction = 2.0 * abs(dy @ (Kxn - Kx))
-            eta_max = movement / interaction if interaction > 0 else np.inf
             k += 1
-            eta_next = min((1.0 - (k + 1) ** (-opts.step_reduction_exp)) * eta_max,
-                           (1.0 + (k + 1) ** (-opts.step_growth_exp)) * eta)
-            ok = ok_own = eta <= eta_max
+            ok_own, eta_max, eta_next = step_size_update(eta, omega, xn - x, yn - y, Kxn - Kx, k, opts)
+            ok = ok_own
             if fixed is not None:
                 ok, eta_next = True, eta
             if sched_a is not None:
-                ok = bool(sched_a[k - 1][2])
+                ok = bool(sched_a[k - 1][1])
             if record:
                 attempt_log.append((eta, omega, int(ok), eta_max, eta_next, int(ok_own)))
             if ok:
@@ -196,11 +232,8 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
             entry.update(restart=False, to_avg=False)
             check_log.append(entry)
             break
-        to_avg = kc_avg < kc_cur
-        kc = kc_avg if to_avg else kc_cur
-        restart = (kc <= opts.beta_sufficient * kkt0) or \
-                  (kc <= opts.beta_necessary * kkt0 and kc > kkt_prev) or \
-                  (since_restart >= opts.beta_artificial * k)
+        restart, to_avg, kc = restart_decision(kc_cur, kc_avg, wsum > 0, kkt0, kkt_prev, since_restart, k,
+                                               opts)
         entry.update(restart_own=restart, to_avg_own=to_avg)
         if sched_c is not None:
             restart, to_avg = bool(sched_c[n_check][0]), bool(sched_c[n_check][1])
@@ -209,10 +242,8 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
         kkt_prev = kc
         if restart:
             xc, yc = (xbar, ybar) if to_avg else (x, y)
-            dxr, dyr = np.linalg.norm(xc - xa), np.linalg.norm(yc - ya)
-            if dxr > 1e-10 and dyr > 1e-10:
-                w = opts.omega_smoothing
-                omega = float(np.exp(w * np.log(dyr / dxr) + (1 - w) * np.log(omega)))
+            omega = primal_weight_update(omega, float(np.linalg.norm(xc - xa)), float(np.linalg.norm(yc - ya)),
+                                         opts.omega_smoothing)
             x, y = xc.copy(), yc.copy()
             Kx, KTy = K @ x, KT @ y
             xa, ya = x.copy(), y.copy()

@@ -29,7 +29,10 @@ def _make_fn():
                 raise pdhg.PDHGError(f"UCRelax forward: solver status {r['status_name']}")
             ctx.relax = relax
             ctx.d_shape = d.shape
-            cost = (ws.t["c"] * x).sum()
+            # pdhg_backward differentiates the workspace's last solve: remember which
+            ctx.generation = ws.generation
+            # the optimal cost c^T x* as the library evaluated it in FP64
+            cost = torch.tensor(r["primal_obj"], dtype=torch.float64, device=ws.device)
             p = x.index_select(0, relax.idx_p).reshape(relax.T, relax.G)
             return cost, p
 
@@ -37,6 +40,10 @@ def _make_fn():
         def backward(ctx, g_cost, g_p):
             relax = ctx.relax
             ws = relax.ws
+            if ws.generation != ctx.generation:
+                raise pdhg.PDHGError(
+                    "UCRelax backward: the workspace was solved again after this forward; "
+                    "run backward before the next forward on the same UCRelax")
             gq = torch.empty(ws.m, dtype=torch.float64, device=ws.device)
             gc = torch.empty(ws.n, dtype=torch.float64, device=ws.device)
             gx_ptr = None

@@ -17,6 +17,7 @@ constexpr int kCheckEvery = 64;  // step attempts between KKT checks (one graph 
 constexpr int kMaxBlocks = 8192; // upper bound of the persistent grid sizes
 constexpr int kRowSums = 4;      // per-candidate sums of the row-side KKT kernel
 constexpr int kColSums = 5;      // per-candidate sums of the column-side KKT kernel
+constexpr int kTraceCheckCols = 12;  // values recorded per KKT check in the trace
 
 // Sliced ELL with 32-row slices over the internal (length-sorted) row order.
 // Entry k of row r = 32 s + lane sits at off[s] + 32 k + lane, so the warp
@@ -102,7 +103,7 @@ struct IterArgs {
   DevState* st;
   double* partials;
   double* trace_a;  // [cap][5]
-  double* trace_c;  // [cap][6]
+  double* trace_c;  // [cap][kTraceCheckCols]
   volatile int32_t* cancel;
   unsigned long long cond;  // cudaGraphConditionalHandle
   int32_t in_graph;

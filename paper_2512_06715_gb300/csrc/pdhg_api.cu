@@ -292,9 +292,9 @@ static int validate_opts(const pdhg_opts* o) {
 static int ensure_trace(Workspace* w) {
   if (!w->opts.trace || w->trace_a) return PDHG_OK;
   w->trace_cap_a = 1 << 16;
-  w->trace_cap_c = 1 << 16;
+  w->trace_cap_c = 1 << 17;
   DALLOC(w->trace_a, w->trace_cap_a * 5);
-  DALLOC(w->trace_c, w->trace_cap_c * 8);
+  DALLOC(w->trace_c, w->trace_cap_c * kTraceCheckCols);
   return PDHG_OK;
 }
 
@@ -488,6 +488,7 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     res->eta = h.eta;
     res->omega = h.omega;
     res->kernel_launches = launches;
+    res->returned_average = h.best_is_avg;
   }
   w->solved = true;
   return h.numeric ? fail(PDHG_ERR_NUMERIC, "NaN/Inf met in a KKT evaluation") : PDHG_OK;
@@ -780,7 +781,7 @@ extern "C" int pdhg_get_trace(void* ws, double* attempts, int64_t cap_a, double*
   if (attempts && ca > 0)
     CK(cudaMemcpy(attempts, w->trace_a, sizeof(double) * 5 * ca, cudaMemcpyDeviceToHost));
   if (checks && cc > 0)
-    CK(cudaMemcpy(checks, w->trace_c, sizeof(double) * 8 * cc, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(checks, w->trace_c, sizeof(double) * kTraceCheckCols * cc, cudaMemcpyDeviceToHost));
   return PDHG_OK;
 }
 

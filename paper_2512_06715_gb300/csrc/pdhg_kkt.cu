@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
   if (st->trace_on && a.trace_c) {
     int64_t t = st->n_trace_c;
     if (t < st->trace_cap_c) {
-      double* r = a.trace_c + t * 8;
+      double* r = a.trace_c + t * kTraceCheckCols;
       r[0] = (double)(st->k_offset + st->k);
       r[1] = (double)restart;
       r[2] = (double)to_avg;
@@ -312,6 +312,10 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
       r[5] = kw[1];
       r[6] = rel[0];
       r[7] = rel[1];
+      r[8] = relp[0];
+      r[9] = reld[0];
+      r[10] = relg[0];
+      r[11] = st->eta;
     }
     st->n_trace_c = t + 1;
   }

@@ -9,6 +9,8 @@
 // only scratch, the per-column statistics of one pass, lives in the fixed
 // file-scope array below; every GPU that loads the library holds it until the
 // process exits.
+#include <cuda.h>  // CUcontext and CUresult types only; the driver calls are fetched at run time
+
 #include <mutex>
 #include <string>
 
@@ -18,14 +20,52 @@ namespace ucpdhg {
 
 // Columns the scratch can hold: 2^21 doubles = 16 MiB per device.
 constexpr int64_t kNoAllocMaxCols = int64_t(1) << 21;
-constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocMaxContexts = 64;
 
 static __device__ __align__(256) double g_colstat[kNoAllocMaxCols];
 
 namespace {
 
+// The device address of g_colstat belongs to a CUDA context, not to a device
+// ordinal: after cudaDeviceReset, or under a driver-API context other than the
+// device's primary one, the address differs.  The cache is therefore keyed by
+// the current context's unique id (cuCtxGetId: ids are never reused within a
+// process), fetched through the runtime's driver entry points so the library
+// does not link against libcuda.
 std::mutex g_noalloc_mutex;
-double* g_noalloc_scratch[kNoAllocMaxDevices] = {nullptr};
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  double* ptr;
+};
+ScratchEntry g_noalloc_scratch[kNoAllocMaxContexts];
+int g_noalloc_entries = 0;
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the calling thread's current context (0 if none or unknown).
+unsigned long long current_context_id() {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess)
+      return 0;
+    g_ctx_get_current = (CtxGetCurrentFn)f1;
+    g_ctx_get_id = (CtxGetIdFn)f2;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int noalloc_fail(int code, const std::string& msg) {
   g_err = msg;  // reported by pdhg_last_error()
@@ -116,22 +156,28 @@ extern "C" int pdhg_rescale_noalloc(const pdhg_problem* prob, int32_t ruiz_iters
                             " exceeds the fixed scratch of " + std::to_string(kNoAllocMaxCols) +
                             " columns");
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0)
     return noalloc_fail(PDHG_ERR_CUDA, "pdhg_rescale_noalloc: no usable current device");
   double* colstat = nullptr;
   {
-    // Once per device, with that device current: the device address of the
+    // Once per context, with its device current: the device address of the
     // file-scope scratch (its host-side name is only a stand-in).
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_scratch[dev]) {
+    unsigned long long id = current_context_id();
+    for (int k = 0; id != 0 && k < g_noalloc_entries; ++k)
+      if (g_noalloc_scratch[k].ctx_id == id) colstat = g_noalloc_scratch[k].ptr;
+    if (!colstat) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_colstat);
       if (e != cudaSuccess || !p)
         return noalloc_fail(PDHG_ERR_CUDA, std::string("pdhg_rescale_noalloc: cudaGetSymbolAddress: ") +
                                                cudaGetErrorString(e));
-      g_noalloc_scratch[dev] = (double*)p;
+      colstat = (double*)p;
+      // the lookup above made the runtime's context current if none was
+      if (id == 0) id = current_context_id();
+      if (id != 0 && g_noalloc_entries < kNoAllocMaxContexts)
+        g_noalloc_scratch[g_noalloc_entries++] = {id, colstat};
     }
-    colstat = g_noalloc_scratch[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = prob->n, m = prob->m;

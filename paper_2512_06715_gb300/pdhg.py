@@ -46,7 +46,7 @@ class pdhg_result(C.Structure):
                 ("rel_kkt", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("solve_seconds", C.c_double), ("time_to_tol", C.c_double * 3),
                 ("iters_to_tol", C.c_int64 * 3), ("eta", C.c_double), ("omega", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("returned_average", C.c_int32), ("reserved", C.c_int32)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -153,6 +153,7 @@ class Workspace:
         self.prob = pdhg_problem(self.n, self.m, self.m_eq, int(self.t["col"].numel()),
                                  *(self.t[k].data_ptr() for k in ("row_ptr", "col", "val", "c", "l", "u", "q")))
         self.opts = opts if opts is not None else default_opts()
+        self.generation = 0  # solves run on this workspace (pdhg_backward differentiates the last)
         self.ws = C.c_void_p()
         with torch.cuda.device(dev):
             _check(lib().pdhg_workspace_create(C.byref(self.prob), C.byref(self.opts), C.byref(self.ws),
@@ -187,6 +188,7 @@ class Workspace:
         x = x_out if x_out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
         y = y_out if y_out is not None else torch.empty(self.m, dtype=torch.float64, device=self.device)
         r = pdhg_result()
+        self.generation += 1
         _check(lib().pdhg_solve(self.ws, x.data_ptr(), y.data_ptr(), C.byref(r), _stream_ptr(stream)),
                "pdhg_solve")
         return x, y, r.to_dict()
@@ -201,6 +203,7 @@ class Workspace:
         x = torch.empty((B, self.n), dtype=torch.float64, device=self.device)
         y = torch.empty((B, self.m), dtype=torch.float64, device=self.device) if want_y else None
         res = (pdhg_result * B)()
+        self.generation += 1
         _check(lib().pdhg_solve_batched(self.ws, B, l_b.data_ptr(), u_b.data_ptr(), x.data_ptr(),
                                         y.data_ptr() if y is not None else None, res, _stream_ptr(stream)),
                "pdhg_solve_batched")
@@ -225,9 +228,9 @@ class Workspace:
                                   _stream_ptr(stream)), "pdhg_apply_K")
         return out
 
-    def trace(self, cap_a=1 << 16, cap_c=1 << 16):
+    def trace(self, cap_a=1 << 16, cap_c=1 << 17):
         a = np.zeros((cap_a, 5))
-        c = np.zeros((cap_c, 8))
+        c = np.zeros((cap_c, 12))
         na, nc = C.c_int64(), C.c_int64()
         _check(lib().pdhg_get_trace(self.ws, a.ctypes.data, cap_a, c.ctypes.data, cap_c, C.byref(na),
                                     C.byref(nc)), "pdhg_get_trace")

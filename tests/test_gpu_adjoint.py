@@ -138,4 +138,11 @@ def test_autograd_function():
     (cost + 0.0 * p.sum()).backward()
     assert np.allclose(d.grad.cpu().numpy(), sx.y[bal], atol=1e-6 * np.abs(sx.y[bal]).max())
     assert np.allclose(ct.grad.cpu().numpy(), sx.x, atol=1e-6 * np.abs(sx.x).max())
+    # backward differentiates the workspace's last solve, so a graph whose
+    # workspace was solved again after its forward is refused
+    cost1, _ = relax(d, ct)
+    cost2, _ = relax(d, ct)
+    with pytest.raises(RuntimeError, match="solved again"):
+        cost1.backward()
+    cost2.backward()
     relax.close()

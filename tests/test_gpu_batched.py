@@ -21,24 +21,28 @@ def _node_lp(inst, l, u):
     return lp_from_arrays(inst.row_ptr, inst.col, inst.val, inst.q, inst.c, l, u, inst.m_eq)
 
 
-@pytest.mark.parametrize("B,tol", [(1, 1e-8), (8, 1e-8), (33, 1e-6)])
+@pytest.mark.parametrize("B,tol", [(1, 1e-8), (8, 1e-8), (33, 1e-8), (64, 1e-8)])
 def test_batched_matches_single_solves(B, tol):
-    """Each node of the batch agrees with the same node solved alone (objective
-    within 100 tol relative) and the oracle recomputes its rel-KKT <= 2 tol.
-    B = 33 runs the 64-slot layout with 31 idle slots."""
+    """Every node of the batch reaches rel-KKT <= 1.5 tol as the oracle
+    recomputes it from the returned point, with violation <= 100 tol; up to 8
+    nodes spread over the batch agree with the same node solved alone (objective
+    within 100 tol relative).  B = 33 runs the 64-slot layout with 31 idle slots,
+    B = 64 a full batch."""
     from paper_2512_06715_gb300.pdhg import Workspace, default_opts
     inst = build_instance(12, 18, 10, 12, seed=3, with_slack=True)
     l_b, u_b = node_fixings(inst, B)
-    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=tol, time_limit_s=120.0))
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=tol, time_limit_s=300.0))
     xb, yb, rb = ws.solve_batched(l_b, u_b)
     xb, yb = xb.cpu().numpy(), yb.cpu().numpy()
-    check = range(B) if B <= 8 else [0, 1, B // 2, B - 1]
-    for k in check:
+    alone = set(np.linspace(0, B - 1, min(B, 8)).round().astype(int).tolist())
+    for k in range(B):
         assert rb[k]["status_name"] == "optimal", (k, rb[k])
         lp = _node_lp(inst, l_b[k], u_b[k])
         c = kkt(lp, xb[k], yb[k])
-        assert c.rel_kkt <= 2 * tol, (k, c.rel_kkt, rb[k]["rel_kkt"])
+        assert c.rel_kkt <= 1.5 * tol, (k, c.rel_kkt, rb[k]["rel_kkt"])
         assert max_violation(lp, xb[k]) <= 100 * tol * max(1.0, np.abs(lp.q).max())
+        if k not in alone:
+            continue
         # the same node solved alone
         single = Workspace(inst.row_ptr, inst.col, inst.val, inst.c, l_b[k], u_b[k], inst.q, inst.m_eq,
                            default_opts(precision="mixed", tol=tol, time_limit_s=120.0))
@@ -52,16 +56,15 @@ def test_batched_matches_single_solves(B, tol):
 
 def test_batched_nodes_bound_the_root():
     """Fixing commitments only tightens the relaxation: every node's optimum is
-    at least the root LP optimum.  Solved to rel-KKT 1e-6 (the gap term bounds
-    each objective's error to ~1e-6 relative, hence the 1e-5 slack); the 1e-8
-    tail of some nodes is slow for PDLP and not what this property is about."""
+    at least the root LP optimum (all solved to rel-KKT 1e-8, whose gap term
+    bounds each objective's relative error by ~1e-8, hence the 1e-7 slack)."""
     from paper_2512_06715_gb300.pdhg import Workspace, default_opts
     inst = build_instance(12, 18, 10, 12, seed=4, with_slack=True)
     l_b, u_b = node_fixings(inst, 16, seed0=2000)
-    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=1e-6, time_limit_s=120.0))
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=1e-8, time_limit_s=300.0))
     _, _, root = ws.solve()
     xb, yb, rb = ws.solve_batched(l_b, u_b)
     assert all(r["status_name"] == "optimal" for r in rb), [r["status_name"] for r in rb]
     for r in rb:
-        assert r["primal_obj"] >= root["primal_obj"] * (1 - 1e-5)
+        assert r["primal_obj"] >= root["primal_obj"] * (1 - 1e-7)
     ws.close()

@@ -190,7 +190,7 @@ def test_pdhg_replay_reproduces_run():
     inst = build_instance(3, 3, 3, 2, seed=0)
     lp = instance_lp(inst)
     a = pdhg_solve(lp, tol=1e-30, stop_after=192, record=True)
-    sched = dict(attempts=[(e[0], e[1], e[2]) for e in a.attempt_log],
+    sched = dict(attempts=[(e[0], e[2]) for e in a.attempt_log],
                  checks=[(c["restart"], c["to_avg"]) for c in a.check_log])
     b = pdhg_solve(lp, tol=1e-30, stop_after=192, schedule=sched)
     assert np.array_equal(a.x_scaled, b.x_scaled) and np.array_equal(a.y_scaled, b.y_scaled)

@@ -2,10 +2,14 @@
 the 6717-bus, 96-period relaxation (n = 1.03 M, m = 3.08 M, nnz = 10.5 M) with
 the autotuned launch configuration the bench uses.
 
-- Constant-step attempts: 64 attempts on the GPU against the oracle's 64 attempts
-  on the same LP (the oracle finishes them in seconds at this size); FP64 to 1e-9
-  and FP32 to 1e-4 (a float32 emulation of the same 64 attempts on the CPU is
-  within 2e-6), relative to the largest entry.
+- Constant-step attempts: 128 attempts on the GPU against the oracle's 128
+  attempts on the same LP (the oracle finishes them in seconds at this size);
+  FP64 to 1e-10 and FP32 to 1e-4 (a float32 emulation of the same attempts on
+  the CPU is within 2e-6), relative to the largest entry, against the candidate
+  (current or average) the GPU reports it returned.
+- Adaptive steps and restarts: 192 attempts in FP64 replayed in the oracle
+  (step sizes and decisions from the GPU, primal weight the oracle's own), to
+  1e-10 relative.
 - The FP64 rel-KKT the GPU reports for its returned point, after a short adaptive
   solve in mixed precision, equals the oracle's recomputation from that point (a
   property of the check reductions that holds at any size)."""
@@ -16,6 +20,7 @@ from oracle.lp import kkt
 from oracle.pdhg import pdhg_solve
 from oracle.scaling import rescale
 from tests.conftest import instance_lp
+from tests.parity_helpers import rel_err, replay_and_compare, returned_candidate
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -38,27 +43,33 @@ def full():
     # attempts and the comparison measures rounding, not amplification
     eta = 0.9
     omega = np.linalg.norm(slp.c) / np.linalg.norm(slp.q)
-    ref = pdhg_solve(lp, fixed=dict(eta=eta, omega=omega), stop_after=64)
+    ref = pdhg_solve(lp, fixed=dict(eta=eta, omega=omega), stop_after=FIXED_ATTEMPTS)
     return inst, lp, eta, omega, ref
 
 
-def _rel_err(x, y, ref):
-    cands = [(ref.x_cur, ref.y_cur), (ref.x_avg, ref.y_avg)]
-    return min(max(np.abs(x - a).max() / np.abs(a).max(), np.abs(y - b).max() / np.abs(b).max())
-               for a, b in cands)
+FIXED_ATTEMPTS = 128
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
 def test_fixed_steps_full_size(full, precision, tol):
     from paper_2512_06715_gb300.pdhg import Workspace, default_opts
     inst, lp, eta, omega, ref = full
     ws = Workspace.from_instance(inst, default_opts(precision=precision, fixed_eta=eta, fixed_omega=omega,
-                                                    max_iters=64, tol=1e-30, time_limit_s=120.0))
+                                                    max_iters=FIXED_ATTEMPTS, tol=1e-30, time_limit_s=120.0))
     x, y, r = ws.solve()
     ws.close()
-    assert r["iterations"] == 64 and r["restarts"] == 0
-    err = _rel_err(x.cpu().numpy(), y.cpu().numpy(), ref)
+    assert r["iterations"] == FIXED_ATTEMPTS and r["restarts"] == 0
+    err = rel_err(x.cpu().numpy(), y.cpu().numpy(), returned_candidate(lp, ref, r))
     assert err <= tol, err
+
+
+def test_adaptive_replay_full_size(full):
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst, lp, _, _, _ = full
+    ws = Workspace.from_instance(inst, default_opts(precision="fp64", max_iters=192, tol=1e-30, trace=1,
+                                                    time_limit_s=120.0))
+    replay_and_compare(ws, lp, 192)
+    ws.close()
 
 
 def test_reported_rel_kkt_full_size(full):
