@@ -75,8 +75,13 @@ def parse():
 # --------------------------------------------------------------------------- helpers
 def algorithmic_bytes(n, m, nnz, elt):
     """Per attempt, CSR-equivalent: matrix stream (value + int32 column + int32 row
-    pointer) of K and K^T, each gathered vector once, each streamed vector once."""
-    dual = nnz * (elt + 4) + 4 * m + 2 * elt * n + elt * m * (6 if elt == 4 else 5)
+    pointer) of K and K^T, each gathered vector once, each streamed vector once.
+    FP32 gathers x and x' (K x recomputed) and streams y_lo; FP64 gathers x' and
+    streams the stored K x in and K x' out."""
+    if elt == 4:
+        dual = nnz * (elt + 4) + 4 * m + 2 * elt * n + elt * m * 6
+    else:
+        dual = nnz * (elt + 4) + 4 * m + elt * n + elt * m * 7
     adj = nnz * (elt + 4) + 4 * n + elt * m + elt * n * 8
     return dual, adj
 
@@ -124,6 +129,16 @@ class ClockSampler:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def dual_kernel_name(variant: int, t: str = "float") -> str:
+    """Template name of the K x' kernel a tuning variant launches (0, 9: the
+    pipelined form; 8, 9: compiled for 8 resident blocks per SM)."""
+    if variant in (0, 9):
+        return f"k_dual_pipe<{t}, {8 if variant == 9 else 1}>"
+    if variant == 8:
+        return f"k_dual<{t}, 1, 8>"
+    return f"k_dual<{t}, {variant}, 1>"
 
 
 def measured_peaks() -> dict:
@@ -316,8 +331,7 @@ def run_ours(args):
     tk = ws.time_kernels(pdhg.PREC_MIXED, reps=20)
     achieved = tk["bytes_dual"] / (tk["ms_dual"] * 1e-3) / 1e9
     peaks = measured_peaks()
-    u_dual = ws.tuning()["fp32"]["unroll_dual"]
-    kname = "k_dual_pipe<float>" if u_dual == 0 else f"k_dual<float, {u_dual}>"
+    kname = dual_kernel_name(ws.tuning()["fp32"]["unroll_dual"])
     traffic = dram_traffic_record(ROOT / "paper_2512_06715_gb300" / "csrc" / "pdhg_kernels.cu", kname)
     roofline = {"bound": "hbm", "kernel": kname + " (K x' + projected dual step)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

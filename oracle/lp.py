@@ -21,6 +21,9 @@ Optimality measures (l2, on the unscaled LP, FP64):
   rel_p    = ||r_p|| / (1 + ||q||),  rel_d = ||r_d|| / (1 + ||c||)
   rel_gap  = |P - D| / (1 + |P| + |D|)
   rel_kkt  = max(rel_p, rel_d, rel_gap)
+
+``ray_check`` tests candidate rays for the infeasibility certificates of the
+same LP (see ``RayCheck``).
 """
 from __future__ import annotations
 
@@ -113,6 +116,53 @@ def kkt(lp: LP, x: np.ndarray, y: np.ndarray) -> KKT:
     rel_d = float(np.linalg.norm(rd) / (1.0 + np.linalg.norm(lp.c)))
     rel_gap = abs(P - D) / (1.0 + abs(P) + abs(D))
     return KKT(P, D, rp, rd, rel_p, rel_d, rel_gap)
+
+
+@dataclass
+class RayCheck:
+    """Certificate test of two candidate rays of the LP (Applegate et al.'s
+    infeasibility detection for PDHG, which the paper's cited PDLP method uses).
+
+    dual ray y (proves primal infeasibility; Farkas):
+      lambda = -K^T y (the dual constraints with c = 0),
+      violations: y_i < 0 on >= rows; lambda_j > 0 where l_j = -inf;
+                  lambda_j < 0 where u_j = +inf,
+      objective  q^T y + sum_j (l_j lambda_j^+ - u_j lambda_j^-) over finite bounds.
+    primal ray x (proves dual infeasibility, i.e. an unbounded LP):
+      violations: (K x)_i != 0 on equality rows, (K x)_i < 0 on >= rows,
+                  x_j < 0 where l_j is finite, x_j > 0 where u_j is finite,
+      objective  c^T x.
+    Violations are measured in the l2 norm of all violated components."""
+    dual_ray_obj: float
+    dual_ray_viol: float
+    primal_ray_obj: float
+    primal_ray_viol: float
+
+    def primal_infeasible(self, eps: float) -> bool:
+        return self.dual_ray_obj > 0.0 and self.dual_ray_viol <= eps * self.dual_ray_obj
+
+    def dual_infeasible(self, eps: float) -> bool:
+        return self.primal_ray_obj < 0.0 and self.primal_ray_viol <= eps * (-self.primal_ray_obj)
+
+
+def ray_check(lp: LP, dx: np.ndarray, dy: np.ndarray) -> RayCheck:
+    lf = np.isfinite(lp.l)
+    uf = np.isfinite(lp.u)
+    ineq = np.arange(lp.m) >= lp.m_eq
+    # dual ray
+    lam = -(lp.K.T @ dy)
+    v_sign = np.where(ineq, np.minimum(dy, 0.0), 0.0)
+    v_lam = np.where(lf, 0.0, np.maximum(lam, 0.0)) + np.where(uf, 0.0, np.minimum(lam, 0.0))
+    d_obj = float(lp.q @ dy + (np.where(lf, lp.l, 0.0) * np.where(lf, np.maximum(lam, 0.0), 0.0)).sum()
+                  - (np.where(uf, lp.u, 0.0) * np.where(uf, np.maximum(-lam, 0.0), 0.0)).sum())
+    d_viol = float(np.sqrt(v_sign @ v_sign + v_lam @ v_lam))
+    # primal ray
+    Kx = lp.K @ dx
+    v_row = np.where(ineq, np.minimum(Kx, 0.0), Kx)
+    v_bnd = np.where(lf, np.minimum(dx, 0.0), 0.0) + np.where(uf, np.maximum(dx, 0.0), 0.0)
+    p_obj = float(lp.c @ dx)
+    p_viol = float(np.sqrt(v_row @ v_row + v_bnd @ v_bnd))
+    return RayCheck(d_obj, d_viol, p_obj, p_viol)
 
 
 def max_violation(lp: LP, x: np.ndarray) -> float:

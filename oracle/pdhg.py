@@ -31,6 +31,15 @@ ones; its code shares nothing with this file):
   the iterate, anchor and KKT_0 move to the candidate (KKT_0 taken with the
   new omega, which also becomes the "previous" value) and the averages reset.
 
+* infeasibility (Applegate et al.'s detection from iterate differences): at
+  every check after the optimality test, the differences since the last
+  restart of the current iterate and of the average, (x_c - x_anchor,
+  y_c - y_anchor) taken back to the unscaled LP, are tested as rays
+  (``oracle.lp.ray_check``): a dual ray with positive objective and violation
+  <= eps_infeasible x objective proves primal infeasibility, a primal ray with
+  negative cost and violation <= eps_infeasible x |cost| dual infeasibility
+  (status "primal_infeasible" / "dual_infeasible"); eps_infeasible = 1e-8.
+
 ``schedule`` replays a recorded run: per attempt (eta, accepted) and per check
 (restart, to_average); the oracle then follows those decisions while still
 computing and returning its own, so that both can be compared.  The primal
@@ -49,7 +58,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .lp import LP, kkt, project_reduced_cost
+from .lp import LP, kkt, project_reduced_cost, ray_check
 from .scaling import rescale
 
 
@@ -64,6 +73,7 @@ class PDLPOptions:
     step_growth_exp: float = 0.6
     ruiz_iters: int = 10
     pock_chambolle: bool = True
+    eps_infeasible: float = 1e-8  # 0 disables the infeasibility test
 
 
 @dataclass
@@ -232,6 +242,22 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
             entry.update(restart=False, to_avg=False)
             check_log.append(entry)
             break
+        if opts.eps_infeasible > 0 and fixed is None:
+            infeasible = None
+            for xc_, yc_ in ((x, y), (xbar, ybar)):
+                rc = ray_check(lp, Dc * (xc_ - xa), Dr * (yc_ - ya))
+                if rc.primal_infeasible(opts.eps_infeasible):
+                    infeasible = "primal_infeasible"
+                elif rc.dual_infeasible(opts.eps_infeasible):
+                    infeasible = "dual_infeasible"
+                if infeasible:
+                    entry.update(ray=rc)
+                    break
+            if infeasible:
+                status = infeasible
+                entry.update(restart=False, to_avg=False)
+                check_log.append(entry)
+                break
         restart, to_avg, kc = restart_decision(kc_cur, kc_avg, wsum > 0, kkt0, kkt_prev, since_restart, k,
                                                opts)
         entry.update(restart_own=restart, to_avg_own=to_avg)

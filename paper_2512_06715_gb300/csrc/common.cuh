@@ -90,6 +90,8 @@ struct IterArgs {
   T* x[2];
   T* y[2];
   T* KTy[2];
+  T* Kx[2];  // K x of x[0], x[1]: stored in FP64 mode (nullptr in FP32 mode, where
+             // k_dual recomputes K x from the matrix pass it makes anyway)
   T* xbar;  // weighted sums (not divided)
   T* ybar;
   T* xa;    // anchors (last restart point)
@@ -262,6 +264,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+
+// FP64 iterations store K x (an m-vector stream read and write per attempt)
+// instead of recomputing it with a second product per matrix entry: GB300's
+// FP64 pipe, not HBM, bounds the FP64 kernels, and the second product costs one
+// FP64 FMA per entry.  FP32 iterations recompute it (FP32 FMAs are nearly free
+// and the stream would cost bandwidth).
+template <class T>
+struct StoresKx {
+  static constexpr bool value = sizeof(T) == 8;
+};
 
 template <class T>
 __device__ __forceinline__ T dual_floor(const T* ylo, int i, int m_eq) {

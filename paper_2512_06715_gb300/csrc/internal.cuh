@@ -28,6 +28,7 @@ struct IterBufs {
   T* x[2] = {nullptr, nullptr};
   T* y[2] = {nullptr, nullptr};
   T* KTy[2] = {nullptr, nullptr};
+  T* Kx[2] = {nullptr, nullptr};  // FP64 only (StoresKx)
   T* xbar = nullptr;
   T* ybar = nullptr;
   T* xa = nullptr;

@@ -7,6 +7,7 @@
 // host launches the graph once per round and waits once per round.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -73,6 +74,7 @@ IterArgs<T> make_args(Workspace* w) {
     a.x[i] = b->x[i];
     a.y[i] = b->y[i];
     a.KTy[i] = b->KTy[i];
+    a.Kx[i] = b->Kx[i];
   }
   a.xbar = b->xbar;
   a.ybar = b->ybar;
@@ -115,6 +117,7 @@ static int alloc_bufs(Workspace* w, IterBufs<T>* b) {
     DALLOC(b->x[i], w->n);
     DALLOC(b->y[i], w->m);
     DALLOC(b->KTy[i], w->n);
+    if (StoresKx<T>::value) DALLOC(b->Kx[i], w->m);
   }
   DALLOC(b->xbar, w->n);
   DALLOC(b->ybar, w->m);
@@ -171,16 +174,21 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
     return PDHG_OK;
   }
   // 1, 2, 4: slices a warp sweeps together; 0: one slice per warp, software
-  // pipelined (the next slice's first entries and row operands load early)
-  const int unrolls[4] = {1, 2, 4, 0};
+  // pipelined (the next slice's first entries and row operands load early);
+  // 8, 9: the one-slice and pipelined forms limited to 32 registers (8 blocks
+  // per SM)
+  const int unrolls[6] = {1, 2, 4, 0, 8, 9};
   const int bps[5] = {2, 3, 4, 6, 8};
+  // UCPDHG_TUNE_LOG=1 prints every timed candidate to stderr
+  const char* log_env = std::getenv("UCPDHG_TUNE_LOG");
+  const bool log = log_env && log_env[0] == '1';
   for (int which = 0; which < 2; ++which) {
     const int nsl = which == 0 ? w->K.nslices : w->KT.nslices;
     float best = 1e30f;
     int bu = 1, bg = which == 0 ? w->grid_k : w->grid_kt;
-    for (int ui = 0; ui < 4; ++ui) {
+    for (int ui = 0; ui < 6; ++ui) {
       const int U = unrolls[ui];
-      const int Us = U > 0 ? U : 1;
+      const int Us = (U == 2 || U == 4) ? U : 1;
       const int need = (nsl + kWarps * Us - 1) / (kWarps * Us);
       for (int bi = 0; bi < 5; ++bi) {
         int g = std::min(w->num_sms * bps[bi], std::min(need, kMaxBlocks));
@@ -201,6 +209,9 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
         CK(cudaEventSynchronize(w->ev[3]));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, w->ev[2], w->ev[3]));
+        if (log)
+          std::fprintf(stderr, "autotune %s %s variant %d grid %d: %.2f us\n", sizeof(T) == 8 ? "fp64" : "fp32",
+                       which == 0 ? "dual" : "adjoint", U, g, ms * 1000.f / 3.f);
         if (ms < best * 0.98f) {
           best = ms;
           bu = U;
@@ -282,8 +293,10 @@ static int validate_opts(const pdhg_opts* o) {
     return fail(PDHG_ERR_INVALID_ARG, "opts: refinement settings out of range");
   if (o->fixed_eta < 0.0 || (o->fixed_eta > 0.0 && !(o->fixed_omega > 0.0)))
     return fail(PDHG_ERR_INVALID_ARG, "opts: fixed_eta needs fixed_omega > 0");
-  if (o->kernel_variant < -1 || o->kernel_variant > 4 || o->kernel_variant == 3)
-    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2 or 4");
+  if (!(o->kernel_variant == -1 || o->kernel_variant == 0 || o->kernel_variant == 1 ||
+        o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 8 ||
+        o->kernel_variant == 9))
+    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8 or 9");
   if (o->kernel_grid < 0 || o->kernel_grid > kMaxBlocks)
     return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_grid out of range");
   return PDHG_OK;
@@ -841,11 +854,14 @@ extern "C" int pdhg_time_kernels(void* ws, int32_t precision, int32_t reps, doub
   const double n = (double)w->n, m = (double)w->m, nnz = (double)w->nnz;
   // algorithmic bytes: CSR-equivalent matrix stream (value + int32 column +
   // int32 row pointer), each gathered vector once, each streamed vector once.
-  // dual: x' and x gathered; y, q, ybar read; ybar, y' written (+ y_lo in FP32 mode)
+  // dual, FP32: x' and x gathered; y, q, y_lo, ybar read; ybar, y' written
+  // dual, FP64: x' gathered; y, q, ybar, K x read; ybar, y', K x' written
   // adjoint: y' gathered; x, xbar, c, l, u read; xbar, K^T y', x'' written
   if (ms_dual) *ms_dual = t_d / reps;
   if (ms_adj) *ms_adj = t_a / reps;
-  if (bytes_dual) *bytes_dual = nnz * (sz + 4.0) + 4.0 * m + 2.0 * sz * n + sz * m * (f32 ? 6.0 : 5.0);
+  if (bytes_dual)
+    *bytes_dual = f32 ? nnz * (sz + 4.0) + 4.0 * m + 2.0 * sz * n + sz * m * 6.0
+                      : nnz * (sz + 4.0) + 4.0 * m + sz * n + sz * m * 7.0;
   if (bytes_adj) *bytes_adj = nnz * (sz + 4.0) + 4.0 * n + sz * m + sz * n * 8.0;
   return PDHG_OK;
 }

@@ -1,8 +1,9 @@
 // The two kernels of one PDHG step attempt (Sec. II.E iteration, PDLP form):
 //
-//   k_dual    : K x' and K x (sliced ELL, warp per 32-row slice, one matrix
-//               pass gathering both) fused with the projected dual step
-//               y' = max(y_lo, y + sigma (q - 2 K x' + K x)),
+//   k_dual    : K x' (sliced ELL, warp per 32-row slice) fused with the
+//               projected dual step y' = max(y_lo, y + sigma (q - 2 K x' + K x));
+//               FP32 recomputes K x in the same matrix pass (gathering x and
+//               x'), FP64 reads the stored K x and writes K x' (StoresKx),
 //               the lazy y-average update, and the FP64 partial sums ||dy||^2 and
 //               dy^T K dx.  The block that finishes last reduces the partials in
 //               fixed order and takes the adaptive step decision (accept/reject,
@@ -161,8 +162,8 @@ __device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, doub
   st->eta = eta_next;
 }
 
-template <class T, int U>
-__global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
+template <class T, int U, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_dual(IterArgs<T> a) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -200,10 +201,19 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
         if (has_pw) yb[u] = a.ybar[i];
       }
     }
-    // K x' and K x in one pass: K x is recomputed instead of stored, which
-    // trades an L2 gather for a stream read and write of m values
+    // FP32: K x' and K x in one pass (K x recomputed: an L2 gather instead of
+    // a stream read and write of m values).  FP64: K x' only, K x read.
     T kx[U], ko[U];
-    sell_dot2_pre<T, U>(a.K, ob, lane, xn, xc, kx, ko);
+    if constexpr (StoresKx<T>::value) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = (s0 + u) * kSlice + lane;
+        ko[u] = i < a.m ? a.Kx[p][i] : (T)0;
+      }
+      sell_dot_pre<T, U>(a.K, ob, lane, xn, kx);
+    } else {
+      sell_dot2_pre<T, U>(a.K, ob, lane, xn, xc, kx, ko);
+    }
 #pragma unroll
     for (int u = 0; u <= U; ++u) ob[u] = nb[u];
 #pragma unroll
@@ -215,6 +225,7 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
         T v = yo[u] + sigma * t;
         if (i >= a.m_eq) v = max(v, lo[u]);
         yn[i] = v;
+        if constexpr (StoresKx<T>::value) a.Kx[1 - p][i] = kx[u];
         if (has_pw) a.ybar[i] = yb[u] + pwT * yo[u];
         const T dy = v - yo[u];
         const T dk = kx[u] - ko[u];
@@ -234,8 +245,8 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterArgs<T> a) {
   }
 }
 
-template <class T, int U>
-__global__ void __launch_bounds__(kBlock) k_adjoint(IterArgs<T> a) {
+template <class T, int U, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_adjoint(IterArgs<T> a) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -363,8 +374,8 @@ __device__ __forceinline__ void staged_dot(const SellView<T>& A, const SliceStag
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_dual_pipe(IterArgs<T> a) {
+template <class T, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_dual_pipe(IterArgs<T> a) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -381,35 +392,43 @@ __global__ void __launch_bounds__(kBlock) k_dual_pipe(IterArgs<T> a) {
   const int nw = (gridDim.x * kBlock) >> 5;
   const int ns = a.K.nslices;
   T acc_dy2 = 0, acc_int = 0;
+  constexpr bool kStored = StoresKx<T>::value;
   // stage the warp's first slice; offsets of the second
   SliceStage<T> cur;
-  T yo, qi, lo, yb;
-  auto row_ops = [&](int s, T& y0, T& q0, T& l0, T& b0) {
+  T yo, qi, lo, yb, kxo;
+  auto row_ops = [&](int s, T& y0, T& q0, T& l0, T& b0, T& k0) {
     const int i = s * kSlice + lane;
-    y0 = q0 = l0 = b0 = 0;
+    y0 = q0 = l0 = b0 = k0 = 0;
     if (s < ns && i < a.m) {
       y0 = yc[i];
       q0 = a.q[i];
       if (i >= a.m_eq) l0 = dual_floor(a.ylo, i, a.m_eq);
       if (has_pw) b0 = a.ybar[i];
+      if (kStored) k0 = a.Kx[p][i];
     }
   };
   {
     const int s = min(gw, ns);
     stage_slice<T>(a.K, __ldg(a.K.off + s), __ldg(a.K.off + min(s + 1, ns)), lane, cur);
-    row_ops(gw, yo, qi, lo, yb);
+    row_ops(gw, yo, qi, lo, yb, kxo);
   }
   int nb0 = __ldg(a.K.off + min(gw + nw, ns)), nb1 = __ldg(a.K.off + min(gw + nw + 1, ns));
   for (int s = gw; s < ns; s += nw) {
     // next slice: entries and row operands; offsets two slices ahead
     SliceStage<T> nxt;
-    T yo2, qi2, lo2, yb2;
+    T yo2, qi2, lo2, yb2, kxo2;
     stage_slice<T>(a.K, nb0, nb1, lane, nxt);
-    row_ops(s + nw, yo2, qi2, lo2, yb2);
+    row_ops(s + nw, yo2, qi2, lo2, yb2, kxo2);
     nb0 = __ldg(a.K.off + min(s + 2 * nw, ns));
     nb1 = __ldg(a.K.off + min(s + 2 * nw + 1, ns));
     T kx, ko;
-    staged_dot<T, true>(a.K, cur, xn, xc, kx, ko);
+    if constexpr (kStored) {
+      T unused;
+      staged_dot<T, false>(a.K, cur, xn, xn, kx, unused);
+      ko = kxo;
+    } else {
+      staged_dot<T, true>(a.K, cur, xn, xc, kx, ko);
+    }
     const int i = s * kSlice + lane;
     if (i < a.m) {
       T t = qi - (T)2 * kx;
@@ -417,6 +436,7 @@ __global__ void __launch_bounds__(kBlock) k_dual_pipe(IterArgs<T> a) {
       T v = yo + sigma * t;
       if (i >= a.m_eq) v = max(v, lo);
       yn[i] = v;
+      if (kStored) a.Kx[1 - p][i] = kx;
       if (has_pw) a.ybar[i] = yb + pwT * yo;
       const T dy = v - yo;
       acc_dy2 += dy * dy;
@@ -427,6 +447,7 @@ __global__ void __launch_bounds__(kBlock) k_dual_pipe(IterArgs<T> a) {
     qi = qi2;
     lo = lo2;
     yb = yb2;
+    kxo = kxo2;
   }
   T acc[2] = {acc_dy2, acc_int};
   if (publish_partials_t<2, T>(acc, a.partials, &st->counter)) {
@@ -439,8 +460,8 @@ __global__ void __launch_bounds__(kBlock) k_dual_pipe(IterArgs<T> a) {
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_adjoint_pipe(IterArgs<T> a) {
+template <class T, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_adjoint_pipe(IterArgs<T> a) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -644,25 +665,38 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
   int gt = (a.KT.nslices + kWarps - 1) / kWarps;
   if (gt > kMaxBlocks) gt = kMaxBlocks;
   k_spmv_into<T><<<gt < 1 ? 1 : gt, kBlock, 0, s>>>(a.KT, a.y[0], a.KTy[0]);
+  if (StoresKx<T>::value) {
+    int gk = (a.K.nslices + kWarps - 1) / kWarps;
+    if (gk > kMaxBlocks) gk = kMaxBlocks;
+    k_spmv_into<T><<<gk < 1 ? 1 : gk, kBlock, 0, s>>>(a.K, a.x[0], a.Kx[0]);
+  }
 }
 
+// Variants: 1, 2, 4 slices per warp; 0 software pipelined; 8 and 9 are the
+// one-slice and the pipelined forms compiled for 8 resident blocks per SM
+// (at most 32 registers, a few spilled to L1) -- more warps in flight against
+// the HBM and L2 latency at the cost of the spills.
 template <class T>
 void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
-    case 0: k_dual_pipe<T><<<grid, kBlock, 0, s>>>(a); break;
-    case 2: k_dual<T, 2><<<grid, kBlock, 0, s>>>(a); break;
-    case 4: k_dual<T, 4><<<grid, kBlock, 0, s>>>(a); break;
-    default: k_dual<T, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 0: k_dual_pipe<T, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 2: k_dual<T, 2, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 4: k_dual<T, 4, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 8: k_dual<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
+    case 9: k_dual_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
+    default: k_dual<T, 1, 1><<<grid, kBlock, 0, s>>>(a); break;
   }
 }
 
 template <class T>
 void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
-    case 0: k_adjoint_pipe<T><<<grid, kBlock, 0, s>>>(a); break;
-    case 2: k_adjoint<T, 2><<<grid, kBlock, 0, s>>>(a); break;
-    case 4: k_adjoint<T, 4><<<grid, kBlock, 0, s>>>(a); break;
-    default: k_adjoint<T, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 0: k_adjoint_pipe<T, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 2: k_adjoint<T, 2, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 4: k_adjoint<T, 4, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 8: k_adjoint<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
+    case 9: k_adjoint_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
+    default: k_adjoint<T, 1, 1><<<grid, kBlock, 0, s>>>(a); break;
   }
 }
 
@@ -672,8 +706,8 @@ void launch_state_init(DevState* st, const RoundInit& r, const double* scalars, 
 
 int blocks_per_sm_iter() {
   int best = 1 << 30;
-  const void* fns[4] = {(const void*)&k_dual<double, 1>, (const void*)&k_adjoint<double, 1>,
-                        (const void*)&k_dual<float, 1>, (const void*)&k_adjoint<float, 1>};
+  const void* fns[4] = {(const void*)&k_dual<double, 1, 1>, (const void*)&k_adjoint<double, 1, 1>,
+                        (const void*)&k_dual<float, 1, 1>, (const void*)&k_adjoint<float, 1, 1>};
   for (const void* f : fns) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0) != cudaSuccess) b = 4;

@@ -339,7 +339,10 @@ __global__ void __launch_bounds__(kBlock) k_restart_apply(IterArgs<T> a) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
     if (t < a.m) {
-      if (to_avg) y[t] = (T)((double)a.ybar[t] / div);
+      if (to_avg) {
+        y[t] = (T)((double)a.ybar[t] / div);
+        if (StoresKx<T>::value) a.Kx[p][t] = (T)a.Kz_avg[t];
+      }
       a.ya[t] = y[t];
       a.ybar[t] = 0;
     }
@@ -415,6 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_recenter(IterArgs<T> a, double f) {
       a.ya[t] = (T)(f * ((double)a.ya[t] - yc));
       a.ybar[t] = (T)(f * ((double)a.ybar[t] - wsum * yc));
       y[t] = 0;
+      if (StoresKx<T>::value) a.Kx[p][t] = 0;  // K x of the new iterate x = 0
     }
     if (t < a.n) {
       const double xc = (double)x[t];
