@@ -58,6 +58,8 @@ extern "C" {
 #define PDHG_STATUS_TIME_LIMIT 3 /* time_limit_s reached (device clock)         */
 #define PDHG_STATUS_CANCELLED 4  /* *cancel_flag became nonzero                 */
 #define PDHG_STATUS_NUMERIC 5    /* NaN/Inf met in a KKT evaluation             */
+#define PDHG_STATUS_PRIMAL_INFEASIBLE 6 /* a dual ray certifies that no x exists  */
+#define PDHG_STATUS_DUAL_INFEASIBLE 7   /* a primal ray certifies an unbounded LP */
 
 /* arithmetic of the iterations (KKT, restart and gap reductions are FP64 always) */
 #define PDHG_PREC_FP64 0  /* FP64 matrix, iterates and accumulation            */
@@ -120,6 +122,22 @@ typedef struct pdhg_opts {
   int32_t kernel_grid;      /* > 0: blocks of both per-attempt kernels, overriding the
                                autotuner's grid; small grids make each warp sweep
                                many slices; 0: default or autotuned; default 0       */
+  double infeas_tol;        /* infeasibility detection (Applegate et al.'s certificates
+                               from iterate differences, the detection of the PDLP
+                               method cited in Sec. II.E): at every check the
+                               differences since the last restart of the current and
+                               the average iterate are tested as rays of the unscaled
+                               LP.  Dual ray y, lambda = -K^T y: objective
+                               q^T y + sum_j (l_j lambda_j^+ - u_j lambda_j^-) over
+                               finite bounds, violation = l2 norm of y_i < 0 on >=
+                               rows and of lambda_j > 0 (l_j = -inf), < 0 (u_j = inf);
+                               primal ray x: objective c^T x, violation = l2 norm of
+                               (Kx)_i != 0 on equality rows, < 0 on >= rows, x_j < 0
+                               (finite l_j), > 0 (finite u_j).  A ray whose violation
+                               is <= infeas_tol x |objective| with the certificate's
+                               sign (dual > 0, primal < 0) ends the solve with
+                               PDHG_STATUS_PRIMAL_INFEASIBLE / _DUAL_INFEASIBLE.
+                               0 disables; default 1e-8                             */
 } pdhg_opts;
 
 /* Outcome of one solve (host struct written by the library). */

@@ -15,8 +15,9 @@ constexpr int kBlock = 256;      // threads per block of every streaming kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kCheckEvery = 64;  // step attempts between KKT checks (one graph body)
 constexpr int kMaxBlocks = 8192; // upper bound of the persistent grid sizes
-constexpr int kRowSums = 4;      // per-candidate sums of the row-side KKT kernel
-constexpr int kColSums = 5;      // per-candidate sums of the column-side KKT kernel
+constexpr int kRowSums = 7;      // per-candidate sums of the row-side KKT kernel
+constexpr int kColSums = 9;      // per-candidate sums of the column-side KKT kernel
+constexpr int kRegionStride = 24;  // doubles per block in each partials region (>= 2 x sums)
 constexpr int kTraceCheckCols = 12;  // values recorded per KKT check in the trace
 
 // Sliced ELL with 32-row slices over the internal (length-sorted) row order.
@@ -65,6 +66,7 @@ struct DevState {
   int64_t k_offset;  // attempts of earlier refinement rounds
   // constants of the method
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
+  double infeas_eps;  // certificate tolerance of the infeasibility test (0: off)
   int32_t fixed;     // constant steps, no restarts
   int32_t art_total; // artificial restart against attempts of all rounds
   int32_t trace_on;
@@ -123,6 +125,10 @@ struct IterArgs {
   const double* iDc;  // 1 / Dc
   double* Kz_avg;   // [m] K~ xbar / wsum (FP64)
   double* KTz_avg;  // [n] K~^T ybar / wsum (FP64)
+  double* Kz_cur;   // [m] K~ x of the current iterate at the last check (FP64)
+  double* KTz_cur;  // [n] K~^T y of the same
+  double* Kx_anc;   // [m] K~ x of the restart anchor (FP64): rays K~ (x - x_anchor)
+  double* KTy_anc;  // [n] K~^T y of the restart anchor
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

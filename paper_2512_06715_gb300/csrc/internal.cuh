@@ -60,6 +60,7 @@ struct RoundInit {
   int64_t trace_cap_a, trace_cap_c;
   int32_t refine;  // 1: refinement rounds (mixed precision)
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
+  double infeas_eps;
 };
 
 // Device-state update of a refinement fold that continues the iteration in
@@ -97,6 +98,7 @@ struct Workspace {
   float *c_f = nullptr, *l_f = nullptr, *u_f = nullptr, *q_f = nullptr, *ylo_f = nullptr;
   double *x_star = nullptr, *y_star = nullptr;
   double *Kz_avg = nullptr, *KTz_avg = nullptr;
+  double *Kz_cur = nullptr, *KTz_cur = nullptr, *Kx_anc = nullptr, *KTy_anc = nullptr;
   double *scr_m = nullptr, *scr_n = nullptr;
   double* scalars = nullptr;  // [16] eta0, omega0, norms, consts
   IterBufs<double> b64;

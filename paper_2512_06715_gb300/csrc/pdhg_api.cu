@@ -104,6 +104,10 @@ IterArgs<T> make_args(Workspace* w) {
   a.iDc = w->iDc;
   a.Kz_avg = w->Kz_avg;
   a.KTz_avg = w->KTz_avg;
+  a.Kz_cur = w->Kz_cur;
+  a.KTz_cur = w->KTz_cur;
+  a.Kx_anc = w->Kx_anc;
+  a.KTy_anc = w->KTy_anc;
   return a;
 }
 
@@ -297,6 +301,8 @@ static int validate_opts(const pdhg_opts* o) {
         o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 8 ||
         o->kernel_variant == 9))
     return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8 or 9");
+  if (!(o->infeas_tol >= 0.0))
+    return fail(PDHG_ERR_INVALID_ARG, "opts: infeas_tol must be >= 0");
   if (o->kernel_grid < 0 || o->kernel_grid > kMaxBlocks)
     return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_grid out of range");
   return PDHG_OK;
@@ -419,6 +425,7 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
       ri.omega_smooth = o.omega_smoothing;
       ri.red_exp = o.step_reduction_exp;
       ri.grow_exp = o.step_growth_exp;
+      ri.infeas_eps = o.infeas_tol;
       if (r == 0 && !w->tune[mixed ? 1 : 0].done) {
         launch_state_init(w->st, ri, w->scalars, s);
         launch_init_iterates<T>(a, 0, s);
@@ -541,6 +548,7 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->cancel_flag = nullptr;
   o->kernel_variant = -1;
   o->kernel_grid = 0;
+  o->infeas_tol = 1e-8;
   return PDHG_OK;
 }
 
@@ -649,12 +657,16 @@ extern "C" int pdhg_workspace_create(const pdhg_problem* prob, const pdhg_opts* 
     A(&w->y_star, m);
     A(&w->Kz_avg, m);
     A(&w->KTz_avg, n);
+    A(&w->Kz_cur, m);
+    A(&w->KTz_cur, n);
+    A(&w->Kx_anc, m);
+    A(&w->KTy_anc, n);
     A(&w->scr_m, m);
     A(&w->scr_n, n);
     A(&w->scalars, 16);
     A(&w->st, 1);
     A(&w->st_backup, 1);
-    A(&w->partials, (size_t)3 * kMaxBlocks * 16);
+    A(&w->partials, (size_t)3 * kMaxBlocks * kRegionStride);
     if (r2 != PDHG_OK) return bail(fail(r2, "device allocation failed"));
   }
   if (cudaMallocHost(&w->st_host, sizeof(DevState)) != cudaSuccess)

@@ -33,7 +33,8 @@ constexpr int kBWarps = 8;            // warps per block of the row/column sweep
 constexpr int kBThreads = kBWarps * 32;
 constexpr int kKktWarps = 4;          // smaller blocks for the FP64 check sweeps
 constexpr int kApplyRows = 4;         // rows per block of the elementwise kernels (x BP threads)
-constexpr int kRowS = 4, kColS = 5;   // per-candidate sums (as in the single-instance check)
+constexpr int kRowS = 7, kColS = 9;   // per-candidate sums (as in the single-instance check,
+                                      // including the infeasibility-ray sums)
 constexpr int kRowsPerWarp = 4;       // rows (columns) a warp sweeps together in kb_dual (kb_adjoint)
 static_assert(kRowsPerWarp == 4 && kSlice % kRowsPerWarp == 0, "int4/float4 entry loads");
 
@@ -62,6 +63,7 @@ struct BGlobal {
   int64_t max_k;
   uint64_t t_start, t_limit_ns;
   double qnorm, cnorm;
+  double infeas_eps;  // certificate tolerance of the infeasibility test (0: off)
   int32_t n_real, all_done;
   uint32_t counter, counter2;
 };
@@ -82,7 +84,8 @@ struct BArgs {
   double *lo, *uo;            // instance bounds l~, u~ (scaled)
   double *Kzc, *Kza;          // K x^ of current / average (FP64)
   double *KTzc, *KTza;        // K^T y^ of current / average
-  const double *c_obj, *q_obj, *iDr, *iDc;  // shared [len]
+  double *Kxa, *KTya;         // K x^, K^T y^ of the restart anchors (infeasibility rays)
+  const double *c_obj, *q_obj, *iDr, *iDc, *Dr, *Dc;  // shared [len]
   BInst* inst;
   BGlobal* g;
   double* part;               // per-block partials
@@ -423,8 +426,12 @@ __global__ void __launch_bounds__(kBThreads) kb_adjoint(BArgs<BP> a) {
 
 // ---------------------------------------------------------------- checks (FP64)
 
+// The infeasibility rays of each instance are the differences of its current
+// and average iterates from its last restart anchor, tested as in the
+// single-instance check (pdhg_kkt.cu): the anchors' FP64 products Kxa, KTya are
+// seeded at the first check and moved at restarts and refinement folds.
 template <int BP>
-__global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_row(BArgs<BP> a) {
+__global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_row(BArgs<BP> a, int init) {
   BGlobal* g = a.g;
   if (g->all_done) return;
   constexpr int H = BP / 32;
@@ -466,7 +473,7 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_row(BArgs<BP> a) {
         if (s_iw[b] > 0.0) d1[h] += v * (double)a.xbar[ci];
       }
     }
-    const double qo = a.q_obj[i], sr0 = a.iDr[i];
+    const double qo = a.q_obj[i], sr0 = a.iDr[i], dr0 = a.Dr[i];
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       const int b = lane + 32 * h;
@@ -482,20 +489,29 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_row(BArgs<BP> a) {
       const double kx_avg = has_avg ? d1[h] * s_iw[b] : d0[h];
       a.Kzc[idx] = d0[h];
       a.Kza[idx] = kx_avg;
+      if (init) a.Kxa[idx] = d0[h];
+      const double kanc = init ? d0[h] : a.Kxa[idx];
       const double y_avg = has_avg ? (double)yb * s_iw[b] : (double)yo;
       const double qr = a.qh[idx], sr = s_idp[b] * sr0;
       const double yanc = (double)a.ya[idx];
+      const bool ineq = i >= a.m_eq;
 #pragma unroll
       for (int cnd = 0; cnd < 2; ++cnd) {
         const double kx = cnd ? kx_avg : d0[h];
         const double yv = cnd ? y_avg : (double)yo;
         double rr = qr - kx;
-        if (i >= a.m_eq) rr = fmax(rr, 0.0);
+        if (ineq) rr = fmax(rr, 0.0);
         const double ru = rr * sr, dd = yv - yanc;
+        const double kdx = (kx - kanc) * sr0;
+        const double vr = ineq ? fmin(kdx, 0.0) : kdx;
+        const double vs = ineq ? fmin(dd, 0.0) * dr0 : 0.0;
         acc[h][cnd * kRowS + 0] += rr * rr;
         acc[h][cnd * kRowS + 1] += ru * ru;
         acc[h][cnd * kRowS + 2] += qo * yv;
         acc[h][cnd * kRowS + 3] += dd * dd;
+        acc[h][cnd * kRowS + 4] += vr * vr;
+        acc[h][cnd * kRowS + 5] += vs * vs;
+        acc[h][cnd * kRowS + 6] += qo * dd;
       }
     }
   }
@@ -504,7 +520,7 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_row(BArgs<BP> a) {
 }
 
 template <int BP>
-__global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_col(BArgs<BP> a) {
+__global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_col(BArgs<BP> a, int init) {
   BGlobal* g = a.g;
   if (g->all_done) return;
   constexpr int H = BP / 32;
@@ -545,7 +561,7 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_col(BArgs<BP> a) {
         if (s_iw[b] > 0.0) e1[h] += v * (double)a.ybar[ci];
       }
     }
-    const double co = a.c_obj[j], sc0 = a.iDc[j];
+    const double co = a.c_obj[j], sc0 = a.iDc[j], dc0 = a.Dc[j];
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       const int b = lane + 32 * h;
@@ -555,6 +571,8 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_col(BArgs<BP> a) {
       const double kty_avg = has_avg ? e1[h] * s_iw[b] : e0[h];
       a.KTzc[idx] = e0[h];
       a.KTza[idx] = kty_avg;
+      if (init) a.KTya[idx] = e0[h];
+      const double kanc = init ? e0[h] : a.KTya[idx];
       const double xc = (double)a.x[s_par[b]][idx];
       const double x_avg = has_avg ? (double)a.xbar[idx] * s_iw[b] : xc;
       const double lo = a.lo[idx], up = a.uo[idx];
@@ -569,11 +587,20 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_col(BArgs<BP> a) {
         const double rd = lam - proj, rdu = rd * sc, lp = proj * s_idd[b];
         const double bnd = (lf ? lo * fmax(lp, 0.0) : 0.0) - (uf ? up * fmax(-lp, 0.0) : 0.0);
         const double dx = xv - xanc;
+        const double lr = kanc - kty, lru = lr * sc0;
+        const double vl = (lf ? 0.0 : fmax(lru, 0.0)) + (uf ? 0.0 : fmin(lru, 0.0));
+        const double bray = (lf ? lo * fmax(lr, 0.0) : 0.0) - (uf ? up * fmax(-lr, 0.0) : 0.0);
+        const double dxu = dx * dc0;
+        const double vb = (lf ? fmin(dxu, 0.0) : 0.0) + (uf ? fmax(dxu, 0.0) : 0.0);
         acc[h][cnd * kColS + 0] += rd * rd;
         acc[h][cnd * kColS + 1] += rdu * rdu;
         acc[h][cnd * kColS + 2] += co * xv;
         acc[h][cnd * kColS + 3] += bnd;
         acc[h][cnd * kColS + 4] += dx * dx;
+        acc[h][cnd * kColS + 5] += vl * vl;
+        acc[h][cnd * kColS + 6] += bray;
+        acc[h][cnd * kColS + 7] += vb * vb;
+        acc[h][cnd * kColS + 8] += co * dx;
       }
     }
   }
@@ -657,6 +684,17 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
           stop = PDHG_STATUS_TIME_LIMIT;
         } else if (a.cancel && *a.cancel) {
           stop = PDHG_STATUS_CANCELLED;
+        } else if (g->infeas_eps > 0.0) {
+          for (int c = 0; c < 2 && !stop; ++c) {
+            const double d_obj = rs[c * kRowS + 6] + cs[c * kColS + 6];
+            const double d_viol = sqrt(rs[c * kRowS + 5] + cs[c * kColS + 5]);
+            const double p_obj = cs[c * kColS + 8];
+            const double p_viol = sqrt(rs[c * kRowS + 4] + cs[c * kColS + 7]);
+            if (d_obj > 0.0 && d_viol <= g->infeas_eps * d_obj)
+              stop = PDHG_STATUS_PRIMAL_INFEASIBLE;
+            else if (p_obj < 0.0 && p_viol <= g->infeas_eps * (-p_obj))
+              stop = PDHG_STATUS_DUAL_INFEASIBLE;
+          }
         }
         if (stop) {
           I.done = 1;
@@ -754,6 +792,7 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
         }
         a.ya[idx] = a.y[p][idx];
         a.ybar[idx] = 0.f;
+        a.Kxa[idx] = I.restart_to_avg ? a.Kza[idx] : a.Kzc[idx];
       } else {
         const double yh = cand_avg ? (double)a.ybar[idx] * iw : (double)a.y[p][idx];
         const double kz = cand_avg ? a.Kza[idx] : a.Kzc[idx];
@@ -774,6 +813,7 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
           a.ybar[idx] = (float)(f * ((double)a.ybar[idx] - wsum * yh));
           a.y[p][idx] = 0.f;
           a.Kx[p][idx] = 0.f;
+          a.Kxa[idx] = f * (a.Kxa[idx] - kz);
         }
         scd += a.q_obj[i] * ys;
       }
@@ -782,6 +822,7 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
     for (int j = blockIdx.x * kApplyRows + r0; j < a.n; j += gridDim.x * kApplyRows) {
       const size_t idx = (size_t)j * BP + b;
       if (restart) {
+        a.KTya[idx] = I.restart_to_avg ? a.KTza[idx] : a.KTzc[idx];
         if (I.restart_to_avg) {
           a.x[p][idx] = (float)((double)a.xbar[idx] / div);
           a.KTy[p][idx] = (float)a.KTza[idx];
@@ -816,6 +857,7 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
           a.uf[idx] = (float)un;
           a.xa[idx] = (float)(f * ((double)a.xa[idx] - xh));
           a.xbar[idx] = (float)(f * ((double)a.xbar[idx] - wsum * xh));
+          a.KTya[idx] = f * (a.KTya[idx] - kz);
           a.KTy[p][idx] = 0.f;
           a.x[p][idx] = 0.f;
           // the pending primal step from the new data (the same step in exact
@@ -1070,6 +1112,7 @@ int setup_batched(Workspace* w, Batched* bt, BArgs<BP>* out) {
   F(&a.cf, n); F(&a.lf, n); F(&a.uf, n); F(&a.qf, m); F(&a.ylf, m);
   D(&a.xst, n); D(&a.yst, m); D(&a.ch, n); D(&a.lh, n); D(&a.uh, n); D(&a.qh, m); D(&a.ylh, m);
   D(&a.lo, n); D(&a.uo, n); D(&a.Kzc, m); D(&a.Kza, m); D(&a.KTzc, n); D(&a.KTza, n);
+  D(&a.Kxa, m); D(&a.KTya, n);
   if (e == cudaSuccess) e = balloc(bt, &bt->inst, BP);
   if (e == cudaSuccess) e = balloc(bt, &bt->g, 1);
   if (e == cudaSuccess) e = balloc(bt, &bt->part, (size_t)3 * 8192 * 64 * 20);
@@ -1093,6 +1136,8 @@ int setup_batched(Workspace* w, Batched* bt, BArgs<BP>* out) {
   a.q_obj = w->q_s;
   a.iDr = w->iDr;
   a.iDc = w->iDc;
+  a.Dr = w->Dr;
+  a.Dc = w->Dc;
   a.inst = bt->inst;
   a.g = bt->g;
   a.part = bt->part;
@@ -1129,8 +1174,8 @@ void launch_body(const BArgs<BP>& a, Batched* bt, cudaStream_t s, int init) {
       kb_adjoint<BP><<<bt->grid_cols, kBThreads, 0, s>>>(a);
     }
   }
-  kb_kkt_row<BP><<<bt->grid_kr, kKktWarps * 32, 0, s>>>(a);
-  kb_kkt_col<BP><<<bt->grid_kc, kKktWarps * 32, 0, s>>>(a);
+  kb_kkt_row<BP><<<bt->grid_kr, kKktWarps * 32, 0, s>>>(a, init);
+  kb_kkt_col<BP><<<bt->grid_kc, kKktWarps * 32, 0, s>>>(a, init);
   kb_control<BP><<<1, 256, 0, s>>>(a, bt->grid_kr, bt->grid_kc, init);
   if (!init) kb_apply<BP><<<bt->grid_apply, kApplyRows * BP, 0, s>>>(a);
 }
@@ -1212,6 +1257,7 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   gin.grow_exp = o.step_growth_exp;
   gin.max_k = o.max_iters;
   gin.t_limit_ns = (uint64_t)(o.time_limit_s * 1e9);
+  gin.infeas_eps = o.infeas_tol;
   gin.n_real = B;
   kb_init_state<<<1, BP < 32 ? 32 : BP, 0, s>>>(bt->inst, bt->g, B, BP, w->scalars, gin);
   const int gv = std::min(w->num_sms * 8, 8192);

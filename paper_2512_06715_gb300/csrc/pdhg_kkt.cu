@@ -22,11 +22,25 @@
 namespace ucpdhg {
 
 __device__ __forceinline__ double* region(double* partials, int r) {
-  return partials + (size_t)r * kMaxBlocks * 16;
+  return partials + (size_t)r * kMaxBlocks * kRegionStride;
 }
 
+// Infeasibility rays.  The differences since the last restart, dx = x - x_anchor
+// and dy = y - y_anchor of each candidate, are tested as rays of the unscaled LP
+// (x = Dc x~, y = Dr y~; K dx = (K~ dx~) / Dr, K^T dy = (K~^T dy~) / Dc).  The
+// products K~ x~ of the anchors are kept (Kx_anc, KTy_anc: set at the first
+// check, moved at restarts and refinement folds) so a ray needs no extra matrix
+// pass: K~ dx~ = K~ x~ - Kx_anc.  A refinement round's coordinates scale every
+// ray by a common factor, which the certificate ratios do not see.
+//
+// Row-side sums per candidate: 0 ||r_p~||^2, 1 ||r_p||^2 (unscaled), 2 q~^T y,
+// 3 ||y - y_anchor||^2, 4 primal-ray row violations^2, 5 dual-ray sign
+// violations^2 (dy < 0 on >= rows), 6 q~^T dy.
+// Column-side: 0 ||r_d~||^2, 1 ||r_d||^2, 2 c~^T x, 3 bound term of D(y),
+// 4 ||x - x_anchor||^2, 5 dual-ray lambda violations^2, 6 bound term of the
+// dual ray, 7 primal-ray bound violations^2, 8 c~^T dx.
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a) {
+__global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a, int init) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -63,21 +77,32 @@ __global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a) {
       }
       const double kx_avg = has_avg ? d1 * iw : d0;
       if (has_avg) a.Kz_avg[i] = kx_avg;
+      a.Kz_cur[i] = d0;
+      if (init) a.Kx_anc[i] = d0;
+      const double kanc = init ? d0 : a.Kx_anc[i];
       const double y_avg = has_avg ? (double)yb * iw : (double)yo;
-      const double qr = a.q_res[i], qo = a.q_obj[i], sr = inv_dp * a.iDr[i];
+      const double qr = a.q_res[i], qo = a.q_obj[i], idr = a.iDr[i], sr = inv_dp * idr;
+      const double dr = a.Dr[i];
       const double yanc = (double)a.ya[i];
+      const bool ineq = i >= a.m_eq;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const double kx = c ? kx_avg : d0;
         const double yv = c ? y_avg : (double)yo;
         double r = qr - kx;
-        if (i >= a.m_eq) r = fmax(r, 0.0);
+        if (ineq) r = fmax(r, 0.0);
         const double ru = r * sr;
         const double dd = yv - yanc;
+        const double kdx = (kx - kanc) * idr;                    // (K dx)_i, unscaled
+        const double vr = ineq ? fmin(kdx, 0.0) : kdx;           // primal-ray row violation
+        const double vs = ineq ? fmin(dd, 0.0) * dr : 0.0;       // dual-ray sign violation
         acc[c * kRowSums + 0] += r * r;
         acc[c * kRowSums + 1] += ru * ru;
         acc[c * kRowSums + 2] += qo * yv;
         acc[c * kRowSums + 3] += dd * dd;
+        acc[c * kRowSums + 4] += vr * vr;
+        acc[c * kRowSums + 5] += vs * vs;
+        acc[c * kRowSums + 6] += qo * dd;
       }
     }
   }
@@ -91,7 +116,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a) {
+__global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a, int init) {
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -122,10 +147,14 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a) {
     if (j < a.n) {
       const double kty_avg = has_avg ? e1 * iw : e0;
       if (has_avg) a.KTz_avg[j] = kty_avg;
+      a.KTz_cur[j] = e0;
+      if (init) a.KTy_anc[j] = e0;
+      const double kanc = init ? e0 : a.KTy_anc[j];
       const double x_avg = has_avg ? (double)a.xbar[j] * iw : (double)xc[j];
       const double lo = a.l_obj[j], up = a.u_obj[j];
       const bool lf = isfinite(lo), uf = isfinite(up);
-      const double cr = a.c_res[j], co = a.c_obj[j], sc = inv_dd * a.iDc[j];
+      const double idc = a.iDc[j], dc = a.Dc[j];
+      const double cr = a.c_res[j], co = a.c_obj[j], sc = inv_dd * idc;
       const double xanc = (double)a.xa[j];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -138,11 +167,23 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a) {
         const double lp = proj * inv_dd;
         const double bnd = (lf ? lo * fmax(lp, 0.0) : 0.0) - (uf ? up * fmax(-lp, 0.0) : 0.0);
         const double dx = xv - xanc;
+        // dual ray: lambda~ = -K~^T dy~ (scaled; l~ lambda~ = l lambda), unscaled / Dc
+        const double lr = kanc - kty;
+        const double lru = lr * idc;
+        const double vl = (lf ? 0.0 : fmax(lru, 0.0)) + (uf ? 0.0 : fmin(lru, 0.0));
+        const double bray = (lf ? lo * fmax(lr, 0.0) : 0.0) - (uf ? up * fmax(-lr, 0.0) : 0.0);
+        // primal ray: dx unscaled = Dc dx~
+        const double dxu = dx * dc;
+        const double vb = (lf ? fmin(dxu, 0.0) : 0.0) + (uf ? fmax(dxu, 0.0) : 0.0);
         acc[c * kColSums + 0] += rd * rd;
         acc[c * kColSums + 1] += rdu * rdu;
         acc[c * kColSums + 2] += co * xv;
         acc[c * kColSums + 3] += bnd;
         acc[c * kColSums + 4] += dx * dx;
+        acc[c * kColSums + 5] += vl * vl;
+        acc[c * kColSums + 6] += bray;
+        acc[c * kColSums + 7] += vb * vb;
+        acc[c * kColSums + 8] += co * dx;
       }
     }
   }
@@ -251,6 +292,22 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     done = 1;
     status = PDHG_STATUS_CANCELLED;
   }
+  if (!done && st->infeas_eps > 0.0 && !st->fixed) {
+    // certificates from the candidates' rays (see the note above k_kkt_row)
+    for (int c = 0; c < 2 && !done; ++c) {
+      const double d_obj = rs[c * kRowSums + 6] + cs[c * kColSums + 6];
+      const double d_viol = sqrt(rs[c * kRowSums + 5] + cs[c * kColSums + 5]);
+      const double p_obj = cs[c * kColSums + 8];
+      const double p_viol = sqrt(rs[c * kRowSums + 4] + cs[c * kColSums + 7]);
+      if (d_obj > 0.0 && d_viol <= st->infeas_eps * d_obj) {
+        done = 1;
+        status = PDHG_STATUS_PRIMAL_INFEASIBLE;
+      } else if (p_obj < 0.0 && p_viol <= st->infeas_eps * (-p_obj)) {
+        done = 1;
+        status = PDHG_STATUS_DUAL_INFEASIBLE;
+      }
+    }
+  }
   int restart = 0, to_avg = 0;
   if (!done && !st->fixed) {
     to_avg = (has_avg && kw[1] < kw[0]) ? 1 : 0;
@@ -345,8 +402,10 @@ __global__ void __launch_bounds__(kBlock) k_restart_apply(IterArgs<T> a) {
       }
       a.ya[t] = y[t];
       a.ybar[t] = 0;
+      a.Kx_anc[t] = to_avg ? a.Kz_avg[t] : a.Kz_cur[t];
     }
     if (t < a.n) {
+      a.KTy_anc[t] = to_avg ? a.KTz_avg[t] : a.KTz_cur[t];
       if (to_avg) {
         x[t] = (T)((double)a.xbar[t] / div);
         a.KTy[p][t] = (T)a.KTz_avg[t];
@@ -419,8 +478,11 @@ __global__ void __launch_bounds__(kBlock) k_recenter(IterArgs<T> a, double f) {
       a.ybar[t] = (T)(f * ((double)a.ybar[t] - wsum * yc));
       y[t] = 0;
       if (StoresKx<T>::value) a.Kx[p][t] = 0;  // K x of the new iterate x = 0
+      // the anchor moves with the coordinates: K x_a' = f (K x_a - K x_c)
+      a.Kx_anc[t] = f * (a.Kx_anc[t] - a.Kz_cur[t]);
     }
     if (t < a.n) {
+      a.KTy_anc[t] = f * (a.KTy_anc[t] - a.KTz_cur[t]);
       const double xc = (double)x[t];
       a.xa[t] = (T)(f * ((double)a.xa[t] - xc));
       a.xbar[t] = (T)(f * ((double)a.xbar[t] - wsum * xc));
@@ -549,8 +611,8 @@ static int vgrid(int64_t n) {
 
 template <class T>
 void launch_check(const IterArgs<T>& a, int grid_k, int grid_kt, int init, cudaStream_t s) {
-  k_kkt_row<T><<<grid_k, kBlock, 0, s>>>(a);
-  k_kkt_col<T><<<grid_kt, kBlock, 0, s>>>(a);
+  k_kkt_row<T><<<grid_k, kBlock, 0, s>>>(a, init);
+  k_kkt_col<T><<<grid_kt, kBlock, 0, s>>>(a, init);
   k_control<T><<<1, kBlock, 0, s>>>(a, grid_k, grid_kt, init);
   if (!init) k_restart_apply<T><<<vgrid(a.n > a.m ? a.n : a.m), kBlock, 0, s>>>(a);
 }

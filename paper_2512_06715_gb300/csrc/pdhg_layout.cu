@@ -373,7 +373,7 @@ void launch_prepare(Workspace* w, cudaStream_t s) {
   k_scale_vals<<<w->grid_kt, kBlock, 0, s>>>(w->KT.v64(), w->KT.val64, w->Dc, w->Dr);
   const int gv = vec_grid(N, sms);
   double* part_vec = w->partials;
-  double* part_max = w->partials + (size_t)kMaxBlocks * 16;
+  double* part_max = w->partials + (size_t)kMaxBlocks * kRegionStride;
   k_scale_vecs<<<gv, kBlock, 0, s>>>(w->c_s, w->l_s, w->u_s, w->q_s, w->Dr, w->Dc, w->n, w->m,
                                      part_vec, w->iDr, w->iDc);
   const int gm = vec_grid(w->K.nnz_pad, sms);

@@ -14,7 +14,8 @@ import numpy as np
 
 PDHG_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NUMERIC", -4: "TIMEOUT", -5: "UNSUPPORTED", -6: "NOMEM"}
-STATUS = {0: "round", 1: "optimal", 2: "iteration_limit", 3: "time_limit", 4: "cancelled", 5: "numeric"}
+STATUS = {0: "round", 1: "optimal", 2: "iteration_limit", 3: "time_limit", 4: "cancelled", 5: "numeric",
+          6: "primal_infeasible", 7: "dual_infeasible"}
 PREC_FP64, PREC_MIXED = 0, 1
 
 
@@ -36,7 +37,7 @@ class pdhg_opts(C.Structure):
                 ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
                 ("bound_obj_rescale", C.c_int32), ("artificial_total", C.c_int32),
                 ("host_loop", C.c_int32), ("autotune", C.c_int32), ("cancel_flag", C.c_void_p),
-                ("kernel_variant", C.c_int32), ("kernel_grid", C.c_int32)]
+                ("kernel_variant", C.c_int32), ("kernel_grid", C.c_int32), ("infeas_tol", C.c_double)]
 
 
 class pdhg_result(C.Structure):
