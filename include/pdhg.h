@@ -138,6 +138,12 @@ typedef struct pdhg_opts {
                                sign (dual > 0, primal < 0) ends the solve with
                                PDHG_STATUS_PRIMAL_INFEASIBLE / _DUAL_INFEASIBLE.
                                0 disables; default 1e-8                             */
+  int32_t ir_fold_checks;   /* mixed: a refinement round also ends after this many
+                               checks without reaching its target, folding the
+                               current iterate into x*, y* all the same, so the FP32
+                               iterate stays a small correction and the per-attempt
+                               changes keep FP32 resolution (0: only at the target);
+                               default 16                                           */
 } pdhg_opts;
 
 /* Outcome of one solve (host struct written by the library). */
@@ -202,6 +208,38 @@ int pdhg_solve_batched(void *ws, int32_t B, const double *l_b, const double *u_b
  *   KKT system on the detected active set. */
 int pdhg_backward(void *ws, double g_cost, const double *g_x, double *grad_q, double *grad_c,
                   void *stream);
+
+/* Active-set polish of the last pdhg_solve (a crossover-lite: the paper's
+ * pipeline passes the PDHG point to a crossover, Sec. III.B).  The active set
+ * is read off the solution -- equality rows, >= rows whose dual exceeds their
+ * slack, variables whose reduced cost exceeds their distance to a bound (held
+ * there) -- and, when it is square (as many active rows as free variables),
+ * the basic solution of that set is computed in FP64 on the device:
+ *   x_B = the bounds,  K_{A,F} x_F = q_A - K_{A,B} x_B,  K_{A,F}^T y_A = c_F,  y = 0 elsewhere
+ * (conjugate gradients on the normal equations with the workspace's matrix,
+ * relative residual 1e-13, one CUDA graph per system).  x_out [n], y_out [m]:
+ * device, original order, may be NULL; written only when the set is square.
+ * *res (host) reports the outcome and the optimality measures of the polished
+ * point (same definitions as pdhg_result, plus the l2 norms of its bound
+ * violations and of negative duals on >= rows; both vanish at an optimal
+ * basis).  A polished point with rel_kkt near 1e-15 is the optimal vertex of
+ * that basis; violations flag a wrongly detected set. */
+#define PDHG_POLISH_OK 1             /* both systems solved                       */
+#define PDHG_POLISH_NOT_SQUARE 2     /* degenerate: active rows != free variables */
+#define PDHG_POLISH_NO_CONVERGENCE 3 /* CG stopped before 1e-13 (singular set?)   */
+typedef struct pdhg_polish_result {
+  int32_t status;                 /* PDHG_POLISH_*                              */
+  int32_t cg_iterations_primal;   /* CG iterations of the two systems           */
+  int32_t cg_iterations_dual;
+  int32_t reserved;
+  int64_t active_rows, free_vars;
+  double rel_p, rel_d, rel_gap, rel_kkt;
+  double primal_obj, dual_obj;
+  double bound_violation;         /* ||max(l - x, 0) + max(x - u, 0)||_2         */
+  double dual_sign_violation;     /* ||min(y_i, 0) over >= rows||_2              */
+} pdhg_polish_result;
+
+int pdhg_polish(void *ws, double *x_out, double *y_out, pdhg_polish_result *res, void *stream);
 
 /* Message of the last failure on this thread ("" if none). */
 const char *pdhg_last_error(void);

@@ -67,6 +67,7 @@ struct DevState {
   // constants of the method
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
   double infeas_eps;  // certificate tolerance of the infeasibility test (0: off)
+  int32_t fold_every; // refinement: fold after this many checks of a round (0: off)
   int32_t fixed;     // constant steps, no restarts
   int32_t art_total; // artificial restart against attempts of all rounds
   int32_t trace_on;

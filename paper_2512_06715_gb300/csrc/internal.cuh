@@ -61,6 +61,7 @@ struct RoundInit {
   int32_t refine;  // 1: refinement rounds (mixed precision)
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
   double infeas_eps;
+  int32_t fold_every;
 };
 
 // Device-state update of a refinement fold that continues the iteration in

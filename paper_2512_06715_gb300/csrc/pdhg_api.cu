@@ -301,6 +301,8 @@ static int validate_opts(const pdhg_opts* o) {
         o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 8 ||
         o->kernel_variant == 9))
     return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8 or 9");
+  if (o->ir_fold_checks < 0)
+    return fail(PDHG_ERR_INVALID_ARG, "opts: ir_fold_checks must be >= 0");
   if (!(o->infeas_tol >= 0.0))
     return fail(PDHG_ERR_INVALID_ARG, "opts: infeas_tol must be >= 0");
   if (o->kernel_grid < 0 || o->kernel_grid > kMaxBlocks)
@@ -426,6 +428,7 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
       ri.red_exp = o.step_reduction_exp;
       ri.grow_exp = o.step_growth_exp;
       ri.infeas_eps = o.infeas_tol;
+      ri.fold_every = o.ir_fold_checks;
       if (r == 0 && !w->tune[mixed ? 1 : 0].done) {
         launch_state_init(w->st, ri, w->scalars, s);
         launch_init_iterates<T>(a, 0, s);
@@ -549,6 +552,7 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->kernel_variant = -1;
   o->kernel_grid = 0;
   o->infeas_tol = 1e-8;
+  o->ir_fold_checks = 16;
   return PDHG_OK;
 }
 

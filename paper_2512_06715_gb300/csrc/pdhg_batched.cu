@@ -46,7 +46,7 @@ struct BInst {
   double kkt0, kkt_prev;
   int32_t restart_now, restart_to_avg;
   int32_t done, status, rounds, act;  // act: takes part in the next attempts
-  int32_t refine, finalize, cand_avg, pad;
+  int32_t refine, finalize, cand_avg, round_checks;  // round_checks: checks this round
   double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
   double round_target;
   double dp, dd;          // Delta_P, Delta_D of the current round
@@ -64,6 +64,7 @@ struct BGlobal {
   uint64_t t_start, t_limit_ns;
   double qnorm, cnorm;
   double infeas_eps;  // certificate tolerance of the infeasibility test (0: off)
+  int32_t fold_every;  // a refinement round also ends after this many checks (0: off)
   int32_t n_real, all_done;
   uint32_t counter, counter2;
 };
@@ -658,6 +659,7 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
         I.round_target = fmax(g->tol, g->red * rel[0]);
       } else {
         I.checks += 1;
+        I.round_checks += 1;
         I.pending_w = 0.0;
         const int best = (has_avg && rel[1] < rel[0]) ? 1 : 0;
         const uint64_t now = globaltimer_ns();
@@ -726,7 +728,8 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
             I.since_restart = 0;
             I.restart_now = 1;
             I.restart_to_avg = to_avg;
-          } else if (rel[0] <= I.round_target) {
+          } else if (rel[0] <= I.round_target ||
+                     (g->fold_every > 0 && I.round_checks >= g->fold_every)) {
             // refinement fold (as pdhg_solve): the current iterate joins x*, y*
             // and kb_apply re-expresses the iteration state in the new
             // coordinates; step size, primal weight, averages and restart
@@ -735,6 +738,7 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
             const double scale = fmin(1.0 / relb, 1e12);
             const double f = scale / I.dp;  // Delta_P = Delta_D here
             I.refine = 1;
+            I.round_checks = 0;
             I.cand_avg = 0;
             I.next_scale = f;
             I.round_target = fmax(g->tol, g->red * relb);
@@ -1258,6 +1262,7 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   gin.max_k = o.max_iters;
   gin.t_limit_ns = (uint64_t)(o.time_limit_s * 1e9);
   gin.infeas_eps = o.infeas_tol;
+  gin.fold_every = o.ir_fold_checks;
   gin.n_real = B;
   kb_init_state<<<1, BP < 32 ? 32 : BP, 0, s>>>(bt->inst, bt->g, B, BP, w->scalars, gin);
   const int gv = std::min(w->num_sms * 8, 8192);

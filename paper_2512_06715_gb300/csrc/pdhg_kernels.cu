@@ -634,6 +634,7 @@ __global__ void k_state_init(DevState* st, RoundInit r, const double* scalars) {
   st->red_exp = r.red_exp;
   st->grow_exp = r.grow_exp;
   st->infeas_eps = r.infeas_eps;
+  st->fold_every = r.fold_every;
   st->fixed = r.fixed;
   st->art_total = r.art_total;
   st->trace_on = r.trace_on;

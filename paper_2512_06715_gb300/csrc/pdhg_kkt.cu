@@ -336,8 +336,12 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
       st->since_restart = 0;
     }
   }
-  if (st->refine && !done && !restart && !st->fixed && rel[0] <= st->round_target) {
-    // Refinement: the current iterate joins x*, y* in FP64 and the round ends;
+  if (st->refine && !done && !restart && !st->fixed &&
+      (rel[0] <= st->round_target || (st->fold_every > 0 && st->checks >= st->fold_every))) {
+    // Refinement: the current iterate joins x*, y* in FP64 and the round ends
+    // (at the round's target, or after fold_every checks: a long round lets
+    // the FP32 iterate grow while its per-attempt changes shrink, until FP32
+    // rounding eats them; folding re-centres it at 0);
     // the host re-expresses the whole iteration state (iterate, pending step,
     // averages, restart anchors) in the new coordinates (k_recenter), so the
     // method continues exactly where it was, with the FP32 values now

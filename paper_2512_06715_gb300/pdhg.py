@@ -37,7 +37,8 @@ class pdhg_opts(C.Structure):
                 ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
                 ("bound_obj_rescale", C.c_int32), ("artificial_total", C.c_int32),
                 ("host_loop", C.c_int32), ("autotune", C.c_int32), ("cancel_flag", C.c_void_p),
-                ("kernel_variant", C.c_int32), ("kernel_grid", C.c_int32), ("infeas_tol", C.c_double)]
+                ("kernel_variant", C.c_int32), ("kernel_grid", C.c_int32), ("infeas_tol", C.c_double),
+                ("ir_fold_checks", C.c_int32)]
 
 
 class pdhg_result(C.Structure):
@@ -57,6 +58,22 @@ class pdhg_result(C.Structure):
         return d
 
 
+class pdhg_polish_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("cg_iterations_primal", C.c_int32),
+                ("cg_iterations_dual", C.c_int32), ("reserved", C.c_int32),
+                ("active_rows", C.c_int64), ("free_vars", C.c_int64),
+                ("rel_p", C.c_double), ("rel_d", C.c_double), ("rel_gap", C.c_double),
+                ("rel_kkt", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
+                ("bound_violation", C.c_double), ("dual_sign_violation", C.c_double)]
+
+    def to_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = POLISH_STATUS.get(self.status, str(self.status))
+        return d
+
+
+POLISH_STATUS = {1: "ok", 2: "not_square", 3: "no_convergence"}
+
 # exported symbols of include/pdhg.h and their signatures
 _SIGS = {
     "pdhg_opts_default": ([C.POINTER(pdhg_opts)], C.c_int),
@@ -69,6 +86,7 @@ _SIGS = {
                             C.POINTER(pdhg_result), C.c_void_p], C.c_int),
     "pdhg_backward": ([C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "pdhg_last_error": ([], C.c_char_p),
+    "pdhg_polish": ([C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(pdhg_polish_result), C.c_void_p], C.c_int),
     "pdhg_prepare": ([C.c_void_p, C.c_void_p], C.c_int),
     "pdhg_get_scaling": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "pdhg_apply_K": ([C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -209,6 +227,20 @@ class Workspace:
                                         y.data_ptr() if y is not None else None, res, _stream_ptr(stream)),
                "pdhg_solve_batched")
         return x, y, [r.to_dict() for r in res]
+
+    def polish(self, stream=None):
+        """Active-set polish of the last solve (pdhg_polish).  Returns (x, y,
+        result dict); x, y are None unless the active set was square."""
+        import torch
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        y = torch.empty(self.m, dtype=torch.float64, device=self.device)
+        r = pdhg_polish_result()
+        _check(lib().pdhg_polish(self.ws, x.data_ptr(), y.data_ptr(), C.byref(r), _stream_ptr(stream)),
+               "pdhg_polish")
+        d = r.to_dict()
+        if d["status_name"] == "not_square":
+            return None, None, d
+        return x, y, d
 
     def prepare(self, stream=None):
         _check(lib().pdhg_prepare(self.ws, _stream_ptr(stream)), "pdhg_prepare")
