@@ -61,8 +61,14 @@ def parse():
     p.add_argument("--kernel-grid", type=int, default=0, help="force the per-attempt kernels' grid")
     p.add_argument("--nodes-workload", default="uc6049_g850_T48_slack",
                    help="shared LP of the batched node relaxations")
+    p.add_argument("--nodes", type=int, default=64, help="node LPs of the batched measurement")
     p.add_argument("--nodes-attempts", type=int, default=640,
                    help="attempts per node of the batched-vs-sequential node throughput (0: skip)")
+    p.add_argument("--nodes-tol", type=float, default=0.0,
+                   help="> 0: solve every node to this rel-KKT instead (converged node LPs/s)")
+    p.add_argument("--nodes-cap", type=float, default=600.0, help="seconds cap of the converged node solves")
+    p.add_argument("--nodes-seq", type=int, default=1,
+                   help="nodes solved one at a time for the sequential comparison")
     p.add_argument("--host-loop", action="store_true",
                    help="launch the per-check bodies from the host instead of one CUDA graph "
                         "(same kernels; profilers cannot see kernels inside conditional graphs)")
@@ -217,20 +223,49 @@ def max_over_ranks(value: float, device) -> float:
     return float(t.item())
 
 
-def node_throughput(args, dev, stream, pdhg):
-    """64 node LPs of one shared K (seeded commitment fixings) advanced by the
-    same number of attempts, batched in one pdhg_solve_batched call and as one
-    node alone: node-attempts per second of both (device time, CUDA events)."""
+def node_partition(B: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous block [start, stop) of the B node LPs that `rank` solves; the
+    blocks of all ranks cover 0..B-1 once and differ in size by at most one.
+    Node LPs are independent, so the partition needs no data exchange."""
+    base, extra = divmod(B, world)
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
+
+
+def gather_node_results(local: list, start: int, world: int) -> list:
+    """Every rank's per-node results, in node order, on every rank (host objects
+    over the process group, once at the end: not a data-path collective)."""
+    if world == 1:
+        return list(local)
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, (start, list(local)))
+    out = []
+    for _, part in sorted(parts, key=lambda p: p[0]):
+        out.extend(part)
+    return out
+
+
+def node_throughput(args, dev, stream, pdhg, world=1, rank=0):
+    """Node LPs of one shared K (64 seeded commitment fixings), partitioned
+    over the ranks (node_partition) and solved by each rank in one
+    pdhg_solve_batched call, against the same nodes solved one at a time.
+    --nodes-tol > 0: every node to that rel-KKT (converged node LPs/s, per-node
+    attempt histogram); else every node advanced --nodes-attempts attempts
+    (node-attempts/s).  Device time with CUDA events, max over ranks."""
     import torch
     from paper_2512_06715_gb300.instances import node_fixings, workload
 
     inst = workload(args.nodes_workload)
-    B, K = 64, args.nodes_attempts
+    B = args.nodes
     l_np, u_np = node_fixings(inst, B)
-    l_b = torch.as_tensor(l_np, device=dev)
-    u_b = torch.as_tensor(u_np, device=dev)
-    o = pdhg.default_opts(precision="mixed", max_iters=K, tol=1e-12, time_limit_s=600.0,
-                          host_loop=int(args.host_loop), autotune=int(not args.no_autotune))
+    start, stop = node_partition(B, world, rank)
+    converged = args.nodes_tol > 0
+    kw = dict(precision="mixed", host_loop=int(args.host_loop), autotune=int(not args.no_autotune))
+    if converged:
+        o = pdhg.default_opts(tol=args.nodes_tol, max_iters=10**9, time_limit_s=args.nodes_cap, **kw)
+    else:
+        o = pdhg.default_opts(tol=1e-12, max_iters=args.nodes_attempts, time_limit_s=600.0, **kw)
 
     def event_time(fn):
         torch.cuda.synchronize()
@@ -241,22 +276,60 @@ def node_throughput(args, dev, stream, pdhg):
         e1.synchronize()
         return e0.elapsed_time(e1) * 1e-3, out
 
-    wb = pdhg.Workspace.from_instance(inst, o, device=dev)
-    wb.solve_batched(l_b, u_b, want_y=False)  # allocations, graph
-    tb, (_, _, rb) = event_time(lambda: wb.solve_batched(l_b, u_b, want_y=False))
-    node_att = sum(r["iterations"] for r in rb)
-    wb.close()
-    w1 = pdhg.Workspace(inst.row_ptr, inst.col, inst.val, inst.c, l_np[0], u_np[0], inst.q, inst.m_eq, o,
-                        device=dev)
-    w1.solve()
-    t1, (_, _, r1) = event_time(lambda: w1.solve())
-    w1.close()
-    nb = node_att / tb
-    ns = r1["iterations"] / t1
-    return {"workload": args.nodes_workload, "n": inst.n, "m": inst.m, "nnz": inst.nnz, "nodes": B,
-            "attempts_per_node": K, "batched_node_attempts_per_s": nb, "sequential_node_attempts_per_s": ns,
-            "ratio": nb / ns, "batched_ms_per_attempt": tb / max(r["iterations"] for r in rb) * 1e3,
-            "note": "node LPs/s = node-attempts/s / attempts per node; equal attempt budgets per node"}
+    local = []
+    tb = 0.0
+    if stop > start:
+        l_b = torch.as_tensor(l_np[start:stop], device=dev)
+        u_b = torch.as_tensor(u_np[start:stop], device=dev)
+        wb = pdhg.Workspace.from_instance(inst, o, device=dev)
+        if not converged:
+            wb.solve_batched(l_b, u_b, want_y=False)  # allocations, graph
+        tb, (_, _, rb) = event_time(lambda: wb.solve_batched(l_b, u_b, want_y=False))
+        wb.close()
+        local = [{"node": start + k, "status": r["status_name"], "attempts": r["iterations"],
+                  "rel_kkt": r["rel_kkt"], "ir_rounds": r["ir_rounds"]} for k, r in enumerate(rb)]
+    tb = max_over_ranks(tb, dev)
+    nodes = gather_node_results(local, start, world)
+    # one node at a time (rank 0): `seq` nodes spread over the batch
+    seq = max(1, min(args.nodes_seq, B))
+    t_seq, att_seq = [], []
+    if rank == 0:
+        for k in np.linspace(0, B - 1, seq).round().astype(int):
+            w1 = pdhg.Workspace(inst.row_ptr, inst.col, inst.val, inst.c, l_np[k], u_np[k], inst.q,
+                                inst.m_eq, o, device=dev)
+            if not converged:
+                w1.solve()
+            t1, (_, _, r1) = event_time(lambda: w1.solve())
+            w1.close()
+            t_seq.append(t1)
+            att_seq.append(r1["iterations"])
+    total_att = sum(n["attempts"] for n in nodes)
+    out = {"workload": args.nodes_workload, "n": inst.n, "m": inst.m, "nnz": inst.nnz, "nodes": B,
+           "ranks": world, "partition": [list(node_partition(B, world, r)) for r in range(world)]}
+    if converged:
+        att = np.array([n["attempts"] for n in nodes])
+        statuses = sorted({n["status"] for n in nodes})
+        t_seq_total = float(np.mean(t_seq)) * B if t_seq else None
+        out.update({"tol": args.nodes_tol, "cap_s": args.nodes_cap, "statuses": statuses,
+                    "optimal": sum(n["status"] == "optimal" for n in nodes),
+                    "batched_s": tb, "batched_node_lps_per_s": B / tb,
+                    "sequential_node_lps_per_s": (B / t_seq_total) if t_seq_total else None,
+                    "ratio": (t_seq_total / tb) if t_seq_total else None,
+                    "sequential_sample": {"nodes": seq, "mean_s": float(np.mean(t_seq)) if t_seq else None,
+                                          "mean_attempts": float(np.mean(att_seq)) if att_seq else None},
+                    "attempts_histogram": {"bins": np.histogram(att, bins=8)[1].round().astype(int).tolist(),
+                                           "counts": np.histogram(att, bins=8)[0].tolist()},
+                    "attempts_min_median_max": [int(att.min()), int(np.median(att)), int(att.max())],
+                    "note": "node LPs/s = nodes / wall time to rel-KKT tol (batched: one call per rank, "
+                            "max over ranks; sequential: mean single mixed solve x nodes)"})
+    else:
+        nb = total_att / tb
+        ns = (sum(att_seq) / sum(t_seq)) if t_seq else None
+        out.update({"attempts_per_node": args.nodes_attempts, "batched_node_attempts_per_s": nb,
+                    "sequential_node_attempts_per_s": ns, "ratio": (nb / ns) if ns else None,
+                    "batched_ms_per_attempt": tb / max(n["attempts"] for n in nodes) * 1e3,
+                    "note": "node-attempts/s at equal attempt budgets per node"})
+    return out
 
 
 def run_ours(args):
@@ -377,7 +450,8 @@ def run_ours(args):
                          "cap_s": args.ttt_limit, "attempts": r["iterations"],
                          "attempts_per_s": r["iterations"] / r["solve_seconds"]}
 
-    nodes = node_throughput(args, dev, stream, pdhg) if args.nodes_attempts > 0 else None
+    nodes = (node_throughput(args, dev, stream, pdhg, world, rank)
+             if (args.nodes_attempts > 0 or args.nodes_tol > 0) else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -92,3 +92,46 @@ def test_dram_traffic_record_matches_kernel_and_source(tmp_path, monkeypatch):
         assert bench.dram_traffic_record(src, "k_dual<float, 4>") is None
     src.write_text("changed")
     assert bench.dram_traffic_record(src, "k_dual<float, 1>") is None
+
+
+def test_node_partition_covers_every_node_once():
+    sys.path.insert(0, str(ROOT))
+    import bench
+    for B in (1, 7, 64, 65):
+        for world in (1, 2, 3, 8):
+            blocks = [bench.node_partition(B, world, r) for r in range(world)]
+            covered = [k for a, b in blocks for k in range(a, b)]
+            assert covered == list(range(B))
+            sizes = [b - a for a, b in blocks]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def _gather_worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, str(ROOT))
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    start, stop = bench.node_partition(9, world, rank)
+    local = [{"node": k, "rank": rank} for k in range(start, stop)]
+    q.put((rank, bench.gather_node_results(local, start, world)))
+    dist.destroy_process_group()
+
+
+def test_node_results_gather_gloo():
+    """Two ranks solve their blocks of 9 nodes; every rank ends with all 9
+    results in node order, each from the rank whose block holds it."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    for rank in (0, 1):
+        assert [d["node"] for d in got[rank]] == list(range(9))
+        assert [d["rank"] for d in got[rank]] == [0] * 5 + [1] * 4
