@@ -197,6 +197,19 @@ WORKLOADS = {
     "uc4224_g600_T24": dict(n_bus=4224, n_line=5900, n_gen=600, n_periods=24),
 }
 
+# The horizons of the GO Challenge 3 divisions the paper solves (Sec. II.B,
+# Table I): D1 a day in 18 steps, D2 two days in 48 steps, D3 a week in 42
+# steps, on each of the three networks (uniform steps here: 24/18 h, 1 h, 4 h).
+GO3_DIVISIONS = {"D1": dict(n_periods=18, horizon_hours=24.0),
+                 "D2": dict(n_periods=48, horizon_hours=48.0),
+                 "D3": dict(n_periods=42, horizon_hours=168.0)}
+GO3_NETWORKS = {"uc4224_g600": dict(n_bus=4224, n_line=5900, n_gen=600),
+                "uc6049_g850": dict(n_bus=6049, n_line=8470, n_gen=850),
+                "uc6717_g1000": dict(n_bus=6717, n_line=9200, n_gen=1000)}
+for _net, _np in GO3_NETWORKS.items():
+    for _div, _dp in GO3_DIVISIONS.items():
+        WORKLOADS[f"{_net}_{_div}"] = dict(**_np, **_dp)
+
 
 def workload(name: str, seed: int = 0) -> UCInstance:
     return build_instance(seed=seed, **WORKLOADS[name])

@@ -105,3 +105,26 @@ def test_deterministic():
     c = workload("uc24_g33_T24", seed=4)
     assert np.array_equal(a.val, b.val) and np.array_equal(a.q, b.q)
     assert not np.array_equal(a.q, c.q)
+
+
+@pytest.mark.parametrize("net", ["uc4224_g600", "uc6049_g850", "uc6717_g1000"])
+def test_go3_division_horizons(net):
+    """The GO3 division workloads (D1: 18 steps over a day, D2: 48 over two
+    days, D3: 42 over a week) build with those horizons and the network's size;
+    the step length sets the minimum up/down windows and the hourly costs."""
+    from paper_2512_06715_gb300.instances import GO3_DIVISIONS, workload
+    sizes = {}
+    for div, d in GO3_DIVISIONS.items():
+        inst = workload(f"{net}_{div}")
+        T = d["n_periods"]
+        assert inst.n_periods == T and inst.idx_p.shape[0] == T
+        assert inst.dt_hours == pytest.approx(d["horizon_hours"] / T)
+        G, N = inst.n_gen, inst.n_bus
+        assert inst.n == T * (4 * G + N)
+        # windows in periods: ceil(h / dt) with h in 2..6 hours
+        assert inst.gen_min_up.max() <= int(np.ceil(6.0 / inst.dt_hours - 1e-9))
+        # p costs are hourly rates times the step length
+        p0 = inst.idx_p[0]
+        assert np.allclose(inst.c[p0], inst.gen_cost * inst.dt_hours)
+        sizes[div] = inst.n
+    assert sizes["D2"] > sizes["D3"] > sizes["D1"]
