@@ -1,0 +1,63 @@
+"""Host logic of the branch-and-bound driver on the CPU: the node LPs of a
+stand-in workspace are solved by the oracle's dense simplex (phase 1 reports
+infeasible nodes as the GPU's certificates would), and the driver must reach
+the MILP optimum found by enumerating every commitment schedule."""
+import numpy as np
+import pytest
+
+from oracle.brute import milp_by_enumeration
+from oracle.lp import LP
+from oracle.simplex import simplex_solve
+from paper_2512_06715_gb300.bnb import branch_and_bound
+from paper_2512_06715_gb300.instances import build_instance
+from tests.conftest import instance_lp
+
+torch = pytest.importorskip("torch")
+
+
+class SimplexNodes:
+    """solve_batched with the shape of pdhg.Workspace's, on the CPU."""
+
+    def __init__(self, lp):
+        self.lp = lp
+        self.device = torch.device("cpu")
+        self.calls = 0
+
+    def solve_batched(self, l_b, u_b, want_y=True):
+        self.calls += 1
+        xs, res = [], []
+        for l, u in zip(l_b.numpy(), u_b.numpy()):
+            sx = simplex_solve(LP(K=self.lp.K, q=self.lp.q, c=self.lp.c, l=l, u=u, m_eq=self.lp.m_eq))
+            if sx.status == "optimal":
+                xs.append(sx.x)
+                res.append({"status_name": "optimal", "primal_obj": sx.obj, "dual_obj": sx.obj, "rel_kkt": 0.0})
+            else:
+                xs.append(np.zeros(self.lp.n))
+                res.append({"status_name": "primal_infeasible", "primal_obj": np.nan, "dual_obj": np.nan,
+                            "rel_kkt": np.nan})
+        return torch.as_tensor(np.stack(xs)), None, res
+
+
+@pytest.mark.parametrize("shape,seed", [((3, 3, 3, 2), 0), ((3, 3, 3, 2), 1), ((4, 4, 3, 3), 2)])
+def test_bnb_logic_reaches_the_enumerated_optimum(shape, seed):
+    inst = build_instance(*shape, seed=seed)
+    lp = instance_lp(inst)
+    best, _ = milp_by_enumeration(lp, inst.idx_u)
+    ws = SimplexNodes(lp)
+    res = branch_and_bound(ws, inst.idx_u, inst.l, inst.u, gap=1e-9)
+    assert res.status == "optimal"
+    assert abs(res.incumbent - best) <= 1e-9 * abs(best)
+    assert res.bound <= res.incumbent
+    assert res.nodes < 2 ** inst.idx_u.size  # the tree prunes
+
+
+def test_bnb_small_batches_and_node_limit():
+    """Batches of 2 nodes give the same optimum; a node limit of 1 stops at the
+    root with a valid bound below the optimum."""
+    inst = build_instance(4, 4, 3, 3, seed=2)
+    lp = instance_lp(inst)
+    best, _ = milp_by_enumeration(lp, inst.idx_u)
+    res = branch_and_bound(SimplexNodes(lp), inst.idx_u, inst.l, inst.u, batch=2, gap=1e-9)
+    assert res.status == "optimal" and abs(res.incumbent - best) <= 1e-9 * abs(best)
+    res = branch_and_bound(SimplexNodes(lp), inst.idx_u, inst.l, inst.u, max_nodes=1, gap=1e-9)
+    assert res.nodes == 1 and res.bound <= best + 1e-9 * abs(best)

@@ -1,0 +1,52 @@
+"""Branch-and-bound over batched GPU node relaxations (paper Sec. II.D, III.B:
+PDHG bounds for the UC MILP's branch-and-bound) against the oracle's MILP
+optimum by enumeration of every commitment schedule."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle.brute import milp_by_enumeration
+from paper_2512_06715_gb300.instances import build_instance
+from tests.conftest import instance_lp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_06715_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("shape,seed", [((3, 3, 3, 2), 0), ((3, 3, 3, 2), 1), ((4, 4, 3, 3), 2)])
+def test_bnb_reaches_the_enumerated_milp_optimum(shape, seed):
+    from paper_2512_06715_gb300.bnb import branch_and_bound
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst = build_instance(*shape, seed=seed)
+    lp = instance_lp(inst)
+    if shape == (3, 3, 3, 2) and seed == 0:
+        with open(os.path.join(GOLDEN, "uc3bus_2periods.json")) as f:
+            best = json.load(f)["milp_optimum"]
+    else:
+        best, _ = milp_by_enumeration(lp, inst.idx_u)
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=1e-9, time_limit_s=120.0))
+    res = branch_and_bound(ws, inst.idx_u, inst.l, inst.u, gap=1e-7)
+    ws.close()
+    assert res.status == "optimal", res
+    assert abs(res.incumbent - best) <= 1e-6 * abs(best), (res.incumbent, best)
+    assert res.bound <= res.incumbent * (1 + 1e-9)
+    # the schedule is a 0/1 commitment that the enumeration also finds optimal
+    assert res.schedule is not None and set(np.unique(res.schedule)) <= {0.0, 1.0}
+    l, u = lp.l.copy(), lp.u.copy()
+    l[inst.idx_u.reshape(-1)] = u[inst.idx_u.reshape(-1)] = res.schedule.reshape(-1)
+    from oracle.lp import LP
+    from oracle.simplex import simplex_solve
+    sx = simplex_solve(LP(K=lp.K, q=lp.q, c=lp.c, l=l, u=u, m_eq=lp.m_eq))
+    assert sx.status == "optimal" and abs(sx.obj - best) <= 1e-6 * abs(best)
