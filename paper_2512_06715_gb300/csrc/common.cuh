@@ -59,6 +59,7 @@ struct DevState {
   double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
   // targets and limits
   double tol, round_target, ir_red;
+  double round_rel0;  // rel_kkt of the current iterate when the round started
   int64_t max_k, max_checks;
   uint64_t t_start, t_limit_ns;
   double t_tol[3];
@@ -95,8 +96,15 @@ struct IterArgs {
   T* KTy[2];
   T* Kx[2];  // K x of x[0], x[1]: stored in FP64 mode (nullptr in FP32 mode, where
              // k_dual recomputes K x from the matrix pass it makes anyway)
-  T* xbar;  // weighted sums (not divided)
+  T* xbar;  // weighted sums (not divided) of the attempts since the last check
   T* ybar;
+  // FP32 mode: the step-weighted sums since the last restart live in FP64; at
+  // every check the window's FP32 sums (<= 64 terms) are added in and cleared.
+  // The sums must stay exact through refinement folds, which re-express them
+  // relative to the current iterate (a cancellation that FP32 sums of up to 10^6
+  // terms cannot survive).  nullptr in FP64 mode (xbar, ybar are FP64 there).
+  double* xbar64;
+  double* ybar64;
   T* xa;    // anchors (last restart point)
   T* ya;
   const T* c;
@@ -264,6 +272,17 @@ __device__ __forceinline__ void final_sum_t(const double* partials, int nblocks,
 // whose FP64 rate is ~1/60 of FP32, and the rule is a heuristic factor.
 __device__ __forceinline__ double step_power(int64_t k1, double e) {
   return (double)exp2f(-(float)e * log2f((float)k1));
+}
+
+// FP32 iterations take tau = eta / omega and sigma = eta * omega in FP32.  When
+// the step-size rule finds no interaction (eta_max = inf, e.g. a primal iterate
+// pinned at its bounds while the dual diverges on an infeasible LP) it grows eta
+// by (1 + (k+1)^-0.6) per attempt, which leaves the FP32 range within ~10^4
+// attempts; capping eta so both stay below 1e30 keeps the diverging iterates
+// finite until the infeasibility certificate is read off them.  The cap is far
+// above any step the rule accepts on a feasible LP (eta <= eta_max ~ 1/||K~||).
+__device__ __forceinline__ double fp32_step_cap(double omega) {
+  return 1e30 / fmax(omega, 1.0 / omega);
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -31,6 +31,8 @@ struct IterBufs {
   T* Kx[2] = {nullptr, nullptr};  // FP64 only (StoresKx)
   T* xbar = nullptr;
   T* ybar = nullptr;
+  double* xbar64 = nullptr;  // FP32 mode only
+  double* ybar64 = nullptr;
   T* xa = nullptr;
   T* ya = nullptr;
   bool allocated = false;

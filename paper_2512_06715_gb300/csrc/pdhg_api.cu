@@ -78,6 +78,8 @@ IterArgs<T> make_args(Workspace* w) {
   }
   a.xbar = b->xbar;
   a.ybar = b->ybar;
+  a.xbar64 = b->xbar64;
+  a.ybar64 = b->ybar64;
   a.xa = b->xa;
   a.ya = b->ya;
   a.n = (int32_t)w->n;
@@ -125,6 +127,10 @@ static int alloc_bufs(Workspace* w, IterBufs<T>* b) {
   }
   DALLOC(b->xbar, w->n);
   DALLOC(b->ybar, w->m);
+  if (sizeof(T) == 4) {
+    DALLOC(b->xbar64, w->n);
+    DALLOC(b->ybar64, w->m);
+  }
   DALLOC(b->xa, w->n);
   DALLOC(b->ya, w->m);
   b->allocated = true;
@@ -474,7 +480,7 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     // Refinement fold: the round's current iterate is now part of x*, y*.
     // Delta_P / Delta_D grow by 1/rel_kkt relative to round 0, so their ratio
     // (and with it the meaning of the primal weight) stays the same.
-    const double rel = std::max(h.rel_kkt, 1e-300);
+    const double rel = (h.rel_kkt > 0.0 && std::isfinite(h.rel_kkt)) ? h.rel_kkt : 1e-300;
     const double scale = std::min(1.0 / rel, 1e12);
     fold = true;
     fold_f = dp0 * scale / dp;

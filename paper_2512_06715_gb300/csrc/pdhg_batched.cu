@@ -49,6 +49,7 @@ struct BInst {
   int32_t refine, finalize, cand_avg, round_checks;  // round_checks: checks this round
   double rel_p, rel_d, rel_gap, rel_kkt, pobj, dobj;
   double round_target;
+  double round_rel0;      // rel_kkt of the current iterate at the round's start
   double dp, dd;          // Delta_P, Delta_D of the current round
   double next_scale;      // Delta' / Delta for the refinement step
   double const_p, const_d;
@@ -76,7 +77,10 @@ struct BArgs {
   int32_t n, m, m_eq, B;
   // FP32 iterate data [len * BP]
   float *x[2], *y[2], *Kx[2], *KTy[2];
-  float *xbar, *ybar, *xa, *ya;
+  float *xbar, *ybar, *xa, *ya;  // xbar, ybar: step-weighted sums since the last check
+  double *xbar64, *ybar64;        // the sums since the last restart (FP64; the window's
+                                  // FP32 sums are added in and cleared at every check,
+                                  // so refinement folds re-express exact sums)
   float *cf, *lf, *uf, *qf, *ylf;
   // FP64 data [len * BP]
   double *xst, *yst;          // accumulated x*, y* (scaled space)
@@ -287,8 +291,10 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
         I.k += 1;
         I.k_total += 1;
         // attempts of all rounds (a refinement round is a change of coordinates)
-        const double eta_next = fmin((1.0 - step_power(I.k_total + 1, g->red_exp)) * eta_max,
-                                     (1.0 + step_power(I.k_total + 1, g->grow_exp)) * eta);
+        const double eta_next =
+            fmin(fmin((1.0 - step_power(I.k_total + 1, g->red_exp)) * eta_max,
+                      (1.0 + step_power(I.k_total + 1, g->grow_exp)) * eta),
+                 fp32_step_cap(omega));
         const int accept = eta <= eta_max;
         if (accept) {
           I.par = 1 - I.par;
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_row(BArgs<BP> a, int in
         if (!s_act[b]) continue;
         const size_t ci = (size_t)c * BP + b;
         d0[h] += v * (double)a.x[s_par[b]][ci];
-        if (s_iw[b] > 0.0) d1[h] += v * (double)a.xbar[ci];
+        if (s_iw[b] > 0.0) d1[h] += v * ((double)a.xbar[ci] + a.xbar64[ci]);
       }
     }
     const double qo = a.q_obj[i], sr0 = a.iDr[i], dr0 = a.Dr[i];
@@ -483,16 +489,16 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_row(BArgs<BP> a, int in
       const bool has_avg = s_iw[b] > 0.0;
       const float yo = a.y[s_par[b]][idx];
       float yb = a.ybar[idx];
-      if (s_pw[b] != 0.0) {
-        yb = yb + (float)s_pw[b] * yo;
-        a.ybar[idx] = yb;
-      }
+      if (s_pw[b] != 0.0) yb = yb + (float)s_pw[b] * yo;
+      const double ybs = (double)yb + a.ybar64[idx];
+      a.ybar64[idx] = ybs;
+      a.ybar[idx] = 0.f;
       const double kx_avg = has_avg ? d1[h] * s_iw[b] : d0[h];
       a.Kzc[idx] = d0[h];
       a.Kza[idx] = kx_avg;
       if (init) a.Kxa[idx] = d0[h];
       const double kanc = init ? d0[h] : a.Kxa[idx];
-      const double y_avg = has_avg ? (double)yb * s_iw[b] : (double)yo;
+      const double y_avg = has_avg ? ybs * s_iw[b] : (double)yo;
       const double qr = a.qh[idx], sr = s_idp[b] * sr0;
       const double yanc = (double)a.ya[idx];
       const bool ineq = i >= a.m_eq;
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_col(BArgs<BP> a, int in
         if (!s_act[b]) continue;
         const size_t ci = (size_t)c * BP + b;
         e0[h] += v * (double)a.y[s_par[b]][ci];
-        if (s_iw[b] > 0.0) e1[h] += v * (double)a.ybar[ci];
+        if (s_iw[b] > 0.0) e1[h] += v * ((double)a.ybar[ci] + a.ybar64[ci]);
       }
     }
     const double co = a.c_obj[j], sc0 = a.iDc[j], dc0 = a.Dc[j];
@@ -575,7 +581,10 @@ __global__ void __launch_bounds__(kKktWarps * 32) kb_kkt_col(BArgs<BP> a, int in
       if (init) a.KTya[idx] = e0[h];
       const double kanc = init ? e0[h] : a.KTya[idx];
       const double xc = (double)a.x[s_par[b]][idx];
-      const double x_avg = has_avg ? (double)a.xbar[idx] * s_iw[b] : xc;
+      const double xbs = (double)a.xbar[idx] + a.xbar64[idx];
+      a.xbar64[idx] = xbs;
+      a.xbar[idx] = 0.f;
+      const double x_avg = has_avg ? xbs * s_iw[b] : xc;
       const double lo = a.lo[idx], up = a.uo[idx];
       const bool lf = isfinite(lo), uf = isfinite(up);
       const double cr = a.ch[idx], sc = s_idd[b] * sc0, xanc = (double)a.xa[idx];
@@ -657,6 +666,7 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
       if (init) {
         I.kkt0 = I.kkt_prev = kw[0];
         I.round_target = fmax(g->tol, g->red * rel[0]);
+        I.round_rel0 = rel[0];
       } else {
         I.checks += 1;
         I.round_checks += 1;
@@ -729,7 +739,8 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
             I.restart_now = 1;
             I.restart_to_avg = to_avg;
           } else if (rel[0] <= I.round_target ||
-                     (g->fold_every > 0 && I.round_checks >= g->fold_every)) {
+                     (g->fold_every > 0 && I.round_checks >= g->fold_every &&
+                      rel[0] <= I.round_rel0)) {
             // refinement fold (as pdhg_solve): the current iterate joins x*, y*
             // and kb_apply re-expresses the iteration state in the new
             // coordinates; step size, primal weight, averages and restart
@@ -742,6 +753,7 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
             I.cand_avg = 0;
             I.next_scale = f;
             I.round_target = fmax(g->tol, g->red * relb);
+            I.round_rel0 = relb;
             I.rounds += 1;
             // KKT_w with the gap weighted back to round-0 units scales by f
             I.kkt0 *= f;
@@ -791,14 +803,15 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
       const size_t idx = (size_t)i * BP + b;
       if (restart) {
         if (I.restart_to_avg) {
-          a.y[p][idx] = (float)((double)a.ybar[idx] / div);
+          a.y[p][idx] = (float)(((double)a.ybar[idx] + a.ybar64[idx]) / div);
           a.Kx[p][idx] = (float)a.Kza[idx];
         }
         a.ya[idx] = a.y[p][idx];
         a.ybar[idx] = 0.f;
+        a.ybar64[idx] = 0.0;
         a.Kxa[idx] = I.restart_to_avg ? a.Kza[idx] : a.Kzc[idx];
       } else {
-        const double yh = cand_avg ? (double)a.ybar[idx] * iw : (double)a.y[p][idx];
+        const double yh = cand_avg ? ((double)a.ybar[idx] + a.ybar64[idx]) * iw : (double)a.y[p][idx];
         const double kz = cand_avg ? a.Kza[idx] : a.Kzc[idx];
         const double ys = a.yst[idx] + yh * idd;
         a.yst[idx] = ys;
@@ -814,7 +827,8 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
             a.ylf[idx] = (float)yl;
           }
           a.ya[idx] = (float)(f * ((double)a.ya[idx] - yh));
-          a.ybar[idx] = (float)(f * ((double)a.ybar[idx] - wsum * yh));
+          a.ybar64[idx] = f * ((double)a.ybar[idx] + a.ybar64[idx] - wsum * yh);
+          a.ybar[idx] = 0.f;
           a.y[p][idx] = 0.f;
           a.Kx[p][idx] = 0.f;
           a.Kxa[idx] = f * (a.Kxa[idx] - kz);
@@ -828,19 +842,20 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
       if (restart) {
         a.KTya[idx] = I.restart_to_avg ? a.KTza[idx] : a.KTzc[idx];
         if (I.restart_to_avg) {
-          a.x[p][idx] = (float)((double)a.xbar[idx] / div);
+          a.x[p][idx] = (float)(((double)a.xbar[idx] + a.xbar64[idx]) / div);
           a.KTy[p][idx] = (float)a.KTza[idx];
         }
         const float x0 = a.x[p][idx];
         a.xa[idx] = x0;
         a.xbar[idx] = 0.f;
+        a.xbar64[idx] = 0.0;
         float v = x0 - tau * (a.cf[idx] - a.KTy[p][idx]);
         v = fminf(fmaxf(v, a.lf[idx]), a.uf[idx]);
         a.x[1 - p][idx] = v;
         const double d = (double)(v - x0);
         sdx += d * d;
       } else {
-        const double xh = cand_avg ? (double)a.xbar[idx] * iw : (double)a.x[p][idx];
+        const double xh = cand_avg ? ((double)a.xbar[idx] + a.xbar64[idx]) * iw : (double)a.x[p][idx];
         const double kz = cand_avg ? a.KTza[idx] : a.KTzc[idx];
         const double xs = a.xst[idx] + xh * idp;
         a.xst[idx] = xs;
@@ -860,7 +875,8 @@ __global__ void __launch_bounds__(kApplyRows * BP) kb_apply(BArgs<BP> a) {
           a.lf[idx] = (float)ln;
           a.uf[idx] = (float)un;
           a.xa[idx] = (float)(f * ((double)a.xa[idx] - xh));
-          a.xbar[idx] = (float)(f * ((double)a.xbar[idx] - wsum * xh));
+          a.xbar64[idx] = f * ((double)a.xbar[idx] + a.xbar64[idx] - wsum * xh);
+          a.xbar[idx] = 0.f;
           a.KTya[idx] = f * (a.KTya[idx] - kz);
           a.KTy[p][idx] = 0.f;
           a.x[p][idx] = 0.f;
@@ -955,6 +971,7 @@ __global__ void kb_setup(BArgs<BP> a, const double* __restrict__ lb, const doubl
       a.x[1][t] = x0;
       a.xa[t] = x0;
       a.xbar[t] = 0.f;
+      a.xbar64[t] = 0.0;
       a.KTy[0][t] = a.KTy[1][t] = 0.f;
     }
     if (t < Nm) {
@@ -967,6 +984,7 @@ __global__ void kb_setup(BArgs<BP> a, const double* __restrict__ lb, const doubl
       a.yst[t] = 0.0;
       a.y[0][t] = a.y[1][t] = 0.f;
       a.ya[t] = a.ybar[t] = 0.f;
+      a.ybar64[t] = 0.0;
     }
   }
 }
@@ -1116,7 +1134,7 @@ int setup_batched(Workspace* w, Batched* bt, BArgs<BP>* out) {
   F(&a.cf, n); F(&a.lf, n); F(&a.uf, n); F(&a.qf, m); F(&a.ylf, m);
   D(&a.xst, n); D(&a.yst, m); D(&a.ch, n); D(&a.lh, n); D(&a.uh, n); D(&a.qh, m); D(&a.ylh, m);
   D(&a.lo, n); D(&a.uo, n); D(&a.Kzc, m); D(&a.Kza, m); D(&a.KTzc, n); D(&a.KTza, n);
-  D(&a.Kxa, m); D(&a.KTya, n);
+  D(&a.Kxa, m); D(&a.KTya, n); D(&a.xbar64, n); D(&a.ybar64, m);
   if (e == cudaSuccess) e = balloc(bt, &bt->inst, BP);
   if (e == cudaSuccess) e = balloc(bt, &bt->g, 1);
   if (e == cudaSuccess) e = balloc(bt, &bt->part, (size_t)3 * 8192 * 64 * 20);

@@ -130,6 +130,7 @@ __device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, doub
   const int64_t kg = st->k_offset + k;
   double eta_next = fmin((1.0 - step_power(kg + 1, st->red_exp)) * eta_max,
                          (1.0 + step_power(kg + 1, st->grow_exp)) * eta);
+  if (sizeof(T) == 4) eta_next = fmin(eta_next, fp32_step_cap(omega));
   int accept = eta <= eta_max;
   if (st->fixed) {
     accept = 1;
@@ -559,6 +560,7 @@ __global__ void k_init_vectors(IterArgs<T> a) {
       a.x[1][t] = v;
       a.xa[t] = v;
       a.xbar[t] = 0;
+      if (a.xbar64) a.xbar64[t] = 0.0;
     }
     if (t < a.m) {
       T v = 0;
@@ -567,6 +569,7 @@ __global__ void k_init_vectors(IterArgs<T> a) {
       a.y[1][t] = v;
       a.ya[t] = v;
       a.ybar[t] = 0;
+      if (a.ybar64) a.ybar64[t] = 0.0;
     }
   }
 }

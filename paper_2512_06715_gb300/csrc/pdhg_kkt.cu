@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a, int init) {
       const double v = __ldg(A.val + slot);
       const int c = __ldg(A.col + slot);
       d0 += v * (double)xc[c];
-      if (has_avg) d1 += v * (double)xb[c];
+      if (has_avg) d1 += v * ((double)xb[c] + (a.xbar64 ? a.xbar64[c] : 0.0));
     }
     const int i = s * kSlice + lane;
     if (i < a.m) {
@@ -75,12 +75,18 @@ __global__ void __launch_bounds__(kBlock) k_kkt_row(IterArgs<T> a, int init) {
         yb = yb + (T)pw * yo;
         a.ybar[i] = yb;
       }
+      double ybs = (double)yb;  // the sum since the last restart
+      if (a.ybar64) {
+        ybs += a.ybar64[i];
+        a.ybar64[i] = ybs;
+        a.ybar[i] = 0;
+      }
       const double kx_avg = has_avg ? d1 * iw : d0;
       if (has_avg) a.Kz_avg[i] = kx_avg;
       a.Kz_cur[i] = d0;
       if (init) a.Kx_anc[i] = d0;
       const double kanc = init ? d0 : a.Kx_anc[i];
-      const double y_avg = has_avg ? (double)yb * iw : (double)yo;
+      const double y_avg = has_avg ? ybs * iw : (double)yo;
       const double qr = a.q_res[i], qo = a.q_obj[i], idr = a.iDr[i], sr = inv_dp * idr;
       const double dr = a.Dr[i];
       const double yanc = (double)a.ya[i];
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a, int init) {
       const double v = __ldg(A.val + slot);
       const int c = __ldg(A.col + slot);
       e0 += v * (double)yc[c];
-      if (has_avg) e1 += v * (double)yb[c];
+      if (has_avg) e1 += v * ((double)yb[c] + (a.ybar64 ? a.ybar64[c] : 0.0));
     }
     const int j = s * kSlice + lane;
     if (j < a.n) {
@@ -150,7 +156,13 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a, int init) {
       a.KTz_cur[j] = e0;
       if (init) a.KTy_anc[j] = e0;
       const double kanc = init ? e0 : a.KTy_anc[j];
-      const double x_avg = has_avg ? (double)a.xbar[j] * iw : (double)xc[j];
+      double xbs = (double)a.xbar[j];  // the sum since the last restart
+      if (a.xbar64) {
+        xbs += a.xbar64[j];
+        a.xbar64[j] = xbs;
+        a.xbar[j] = 0;
+      }
+      const double x_avg = has_avg ? xbs * iw : (double)xc[j];
       const double lo = a.l_obj[j], up = a.u_obj[j];
       const bool lf = isfinite(lo), uf = isfinite(up);
       const double idc = a.iDc[j], dc = a.Dc[j];
@@ -243,6 +255,7 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     // a refinement round ends at a restart whose candidate improves on the
     // round's starting point by the factor ir_red
     st->round_target = st->refine ? fmax(st->tol, st->ir_red * rel[0]) : st->tol;
+    st->round_rel0 = rel[0];
     st->rel_p = relp[0];
     st->rel_d = reld[0];
     st->rel_gap = relg[0];
@@ -337,7 +350,8 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     }
   }
   if (st->refine && !done && !restart && !st->fixed &&
-      (rel[0] <= st->round_target || (st->fold_every > 0 && st->checks >= st->fold_every))) {
+      (rel[0] <= st->round_target ||
+       (st->fold_every > 0 && st->checks >= st->fold_every && rel[0] <= st->round_rel0))) {
     // Refinement: the current iterate joins x*, y* in FP64 and the round ends
     // (at the round's target, or after fold_every checks: a long round lets
     // the FP32 iterate grow while its per-attempt changes shrink, until FP32
@@ -401,22 +415,24 @@ __global__ void __launch_bounds__(kBlock) k_restart_apply(IterArgs<T> a) {
        t += (int64_t)gridDim.x * blockDim.x) {
     if (t < a.m) {
       if (to_avg) {
-        y[t] = (T)((double)a.ybar[t] / div);
+        y[t] = (T)(((double)a.ybar[t] + (a.ybar64 ? a.ybar64[t] : 0.0)) / div);
         if (StoresKx<T>::value) a.Kx[p][t] = (T)a.Kz_avg[t];
       }
       a.ya[t] = y[t];
       a.ybar[t] = 0;
+      if (a.ybar64) a.ybar64[t] = 0.0;
       a.Kx_anc[t] = to_avg ? a.Kz_avg[t] : a.Kz_cur[t];
     }
     if (t < a.n) {
       a.KTy_anc[t] = to_avg ? a.KTz_avg[t] : a.KTz_cur[t];
       if (to_avg) {
-        x[t] = (T)((double)a.xbar[t] / div);
+        x[t] = (T)(((double)a.xbar[t] + (a.xbar64 ? a.xbar64[t] : 0.0)) / div);
         a.KTy[p][t] = (T)a.KTz_avg[t];
       }
       const T x0 = x[t];
       a.xa[t] = x0;
       a.xbar[t] = 0;
+      if (a.xbar64) a.xbar64[t] = 0.0;
       T v = x0 - tau * (a.c[t] - a.KTy[p][t]);
       v = min(max(v, a.l[t]), a.u[t]);
       a.x[1 - p][t] = v;
@@ -446,11 +462,13 @@ __global__ void k_accumulate(IterArgs<T> a, double* x_star, double* y_star) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
     if (t < a.n) {
-      const double xv = avg ? (double)a.xbar[t] / wsum : (double)a.x[p][t];
+      const double xv = avg ? ((double)a.xbar[t] + (a.xbar64 ? a.xbar64[t] : 0.0)) / wsum
+                            : (double)a.x[p][t];
       x_star[t] = x_star[t] + xv * inv_dp;
     }
     if (t < a.m) {
-      const double yv = avg ? (double)a.ybar[t] / wsum : (double)a.y[p][t];
+      const double yv = avg ? ((double)a.ybar[t] + (a.ybar64 ? a.ybar64[t] : 0.0)) / wsum
+                            : (double)a.y[p][t];
       y_star[t] = y_star[t] + yv * inv_dd;
     }
   }
@@ -479,7 +497,12 @@ __global__ void __launch_bounds__(kBlock) k_recenter(IterArgs<T> a, double f) {
     if (t < a.m) {
       const double yc = (double)y[t];
       a.ya[t] = (T)(f * ((double)a.ya[t] - yc));
-      a.ybar[t] = (T)(f * ((double)a.ybar[t] - wsum * yc));
+      if (a.ybar64) {  // FP64 sums (the FP32 window was flushed at the check)
+        a.ybar64[t] = f * (a.ybar64[t] + (double)a.ybar[t] - wsum * yc);
+        a.ybar[t] = 0;
+      } else {
+        a.ybar[t] = (T)(f * ((double)a.ybar[t] - wsum * yc));
+      }
       y[t] = 0;
       if (StoresKx<T>::value) a.Kx[p][t] = 0;  // K x of the new iterate x = 0
       // the anchor moves with the coordinates: K x_a' = f (K x_a - K x_c)
@@ -489,7 +512,12 @@ __global__ void __launch_bounds__(kBlock) k_recenter(IterArgs<T> a, double f) {
       a.KTy_anc[t] = f * (a.KTy_anc[t] - a.KTz_cur[t]);
       const double xc = (double)x[t];
       a.xa[t] = (T)(f * ((double)a.xa[t] - xc));
-      a.xbar[t] = (T)(f * ((double)a.xbar[t] - wsum * xc));
+      if (a.xbar64) {
+        a.xbar64[t] = f * (a.xbar64[t] + (double)a.xbar[t] - wsum * xc);
+        a.xbar[t] = 0;
+      } else {
+        a.xbar[t] = (T)(f * ((double)a.xbar[t] - wsum * xc));
+      }
       x[t] = 0;
       a.KTy[p][t] = 0;
       T v = -tau * a.c[t];
@@ -519,6 +547,7 @@ __global__ void k_state_continue(DevState* st, RoundContinue rc, const double* s
   st->kkt0 *= rc.f;
   st->kkt_prev *= rc.f;
   st->round_target = fmax(st->tol, st->ir_red * rc.rel);
+  st->round_rel0 = rc.rel;
   st->k_offset = rc.k_offset;
   st->k = 0;
   st->max_k = rc.max_k;

@@ -7,9 +7,10 @@ the autotuned launch configuration the bench uses.
   FP64 to 1e-10 and FP32 to 1e-4 (a float32 emulation of the same attempts on
   the CPU is within 2e-6), relative to the largest entry, against the candidate
   (current or average) the GPU reports it returned.
-- Adaptive steps and restarts: 192 attempts in FP64 replayed in the oracle
-  (step sizes and decisions from the GPU, primal weight the oracle's own), to
-  1e-10 relative.
+- Adaptive steps and restarts: the first 128 attempts (two checks, each with a
+  restart and a primal-weight update) in FP64 replayed in the oracle (step sizes
+  and decisions from the GPU, primal weight the oracle's own), to 1e-10
+  relative.
 - The FP64 rel-KKT the GPU reports for its returned point, after a short adaptive
   solve in mixed precision, equals the oracle's recomputation from that point (a
   property of the check reductions that holds at any size)."""
@@ -66,9 +67,9 @@ def test_fixed_steps_full_size(full, precision, tol):
 def test_adaptive_replay_full_size(full):
     from paper_2512_06715_gb300.pdhg import Workspace, default_opts
     inst, lp, _, _, _ = full
-    ws = Workspace.from_instance(inst, default_opts(precision="fp64", max_iters=192, tol=1e-30, trace=1,
+    ws = Workspace.from_instance(inst, default_opts(precision="fp64", max_iters=128, tol=1e-30, trace=1,
                                                     time_limit_s=120.0))
-    replay_and_compare(ws, lp, 192)
+    replay_and_compare(ws, lp, 128)
     ws.close()
 
 
