@@ -32,6 +32,7 @@ CUDA_SOURCES = [
     "pdhg_batched.cu",
     "pdhg_adjoint.cu",
     "pdhg_noalloc.cu",
+    "pdhg_staged.cu",
 ]
 
 

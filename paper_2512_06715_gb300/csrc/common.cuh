@@ -18,6 +18,7 @@ constexpr int kMaxBlocks = 8192; // upper bound of the persistent grid sizes
 constexpr int kRowSums = 7;      // per-candidate sums of the row-side KKT kernel
 constexpr int kColSums = 9;      // per-candidate sums of the column-side KKT kernel
 constexpr int kRegionStride = 24;  // doubles per block in each partials region (>= 2 x sums)
+constexpr int kStageEntries = 3072;  // sliced-ELL entries per shared-memory chunk (staged kernels)
 constexpr int kTraceCheckCols = 12;  // values recorded per KKT check in the trace
 
 // Sliced ELL with 32-row slices over the internal (length-sorted) row order.
@@ -69,6 +70,7 @@ struct DevState {
   double beta_suff, beta_nec, beta_art, omega_smooth, red_exp, grow_exp;
   double infeas_eps;  // certificate tolerance of the infeasibility test (0: off)
   int32_t fold_every; // refinement: fold after this many checks of a round (0: off)
+  int32_t wait_timeout;  // set by a kernel whose bounded wait gave up
   int32_t fixed;     // constant steps, no restarts
   int32_t art_total; // artificial restart against attempts of all rounds
   int32_t trace_on;
@@ -118,6 +120,11 @@ struct IterArgs {
   double* trace_a;  // [cap][5]
   double* trace_c;  // [cap][kTraceCheckCols]
   volatile int32_t* cancel;
+  // chunks of slices staged in shared memory by the staged kernels: chunk c is
+  // slices [kchunks[c], kchunks[c+1]) of K (tchunks: of K^T)
+  const int32_t* kchunks;
+  const int32_t* tchunks;
+  int32_t kchunks_n, tchunks_n;
   unsigned long long cond;  // cudaGraphConditionalHandle
   int32_t in_graph;
   // FP64 data of the KKT evaluation
@@ -305,6 +312,53 @@ template <class T>
 __device__ __forceinline__ T dual_floor(const T* ylo, int i, int m_eq) {
   if (ylo) return ylo[i];
   return (i < m_eq) ? (T)(-INFINITY) : (T)0;
+}
+
+// Adaptive step rule on the device (thread 0 of the last block of k_dual).
+template <class T>
+__device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, double inter) {
+  const double eta = st->eta, omega = st->omega;
+  const double movement = omega * st->dx2 + dy2 / omega;
+  const double interaction = 2.0 * fabs(inter);
+  const double eta_max = interaction > 0.0 ? movement / interaction : INFINITY;
+  const int64_t k = st->k + 1;
+  st->k = k;
+  // attempts of all rounds: a refinement round is a change of coordinates,
+  // not a new solve
+  const int64_t kg = st->k_offset + k;
+  double eta_next = fmin((1.0 - step_power(kg + 1, st->red_exp)) * eta_max,
+                         (1.0 + step_power(kg + 1, st->grow_exp)) * eta);
+  if (sizeof(T) == 4) eta_next = fmin(eta_next, fp32_step_cap(omega));
+  int accept = eta <= eta_max;
+  if (st->fixed) {
+    accept = 1;
+    eta_next = eta;
+  }
+  if (st->trace_on && a.trace_a) {
+    int64_t t = st->n_trace_a;
+    if (t < st->trace_cap_a) {
+      double* r = a.trace_a + t * 5;
+      r[0] = eta;
+      r[1] = omega;
+      r[2] = (double)accept;
+      r[3] = eta_max;
+      r[4] = eta_next;
+    }
+    st->n_trace_a = t + 1;
+  }
+  if (accept) {
+    st->par = 1 - st->par;
+    st->w_last = eta;
+    st->pending_w = eta;
+    st->wsum += eta;
+    st->accepted += 1;
+  } else {
+    st->w_last = 0.0;
+    st->pending_w = 0.0;
+  }
+  st->accepted_last = accept;
+  st->since_restart += 1;
+  st->eta = eta_next;
 }
 
 // ---- host-side launchers (defined in the .cu files) ----------------------------

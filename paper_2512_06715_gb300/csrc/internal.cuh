@@ -18,6 +18,8 @@ struct DevSell {
   int32_t* src = nullptr;  // CSR position of each slot, -1 for padding
   double* val64 = nullptr;
   float* val32 = nullptr;
+  int32_t* chunks = nullptr;  // [nchunks + 1] slice boundaries of the staged chunks
+  int32_t nchunks = 0;        // 0: a slice exceeds kStageEntries (no staged kernels)
   SellView<double> v64() const { return {off, col, val64, nslices, rows}; }
   SellView<float> v32() const { return {off, col, val32, nslices, rows}; }
 };
@@ -149,6 +151,16 @@ template <class T>
 void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll);
 void launch_state_init(DevState* st, const RoundInit& r, const double* scalars, cudaStream_t s);
 int blocks_per_sm_iter();  // resident blocks per SM of the per-attempt kernels (both precisions)
+
+// pdhg_staged.cu: per-attempt kernels with TMA-staged matrix chunks
+template <class T>
+void launch_dual_staged(const IterArgs<T>& a, int grid, cudaStream_t s, int pair);
+template <class T>
+void launch_adjoint_staged(const IterArgs<T>& a, int grid, cudaStream_t s, int pair);
+int staged_setup();
+// chunks of consecutive slices with at most kStageEntries entries each; false if
+// a single slice is larger
+bool build_chunks(const std::vector<int32_t>& off, std::vector<int32_t>* chunks);
 
 // pdhg_kkt.cu
 template <class T>

@@ -90,6 +90,10 @@ IterArgs<T> make_args(Workspace* w) {
   a.trace_a = w->trace_a;
   a.trace_c = w->trace_c;
   a.cancel = w->opts.cancel_flag;
+  a.kchunks = w->K.chunks;
+  a.kchunks_n = w->K.nchunks;
+  a.tchunks = w->KT.chunks;
+  a.tchunks_n = w->KT.nchunks;
   a.cond = 0;
   a.in_graph = 0;
   a.K64 = w->K.v64();
@@ -179,6 +183,10 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   t.grid_dual = w->grid_k;
   t.grid_adj = w->grid_kt;
   if (!w->opts.autotune || fixed_variant >= 0) {
+    if (fixed_variant >= 16 &&
+        (w->K.nchunks == 0 || w->KT.nchunks == 0 || staged_setup() != 0))
+      return fail(PDHG_ERR_UNSUPPORTED,
+                  "kernel_variant 16/17: a slice exceeds the staged chunk size on this matrix");
     if (w->opts.kernel_grid > 0) t.grid_dual = t.grid_adj = w->opts.kernel_grid;
     t.done = true;
     return PDHG_OK;
@@ -187,7 +195,8 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   // pipelined (the next slice's first entries and row operands load early);
   // 8, 9: the one-slice and pipelined forms limited to 32 registers (8 blocks
   // per SM)
-  const int unrolls[6] = {1, 2, 4, 0, 8, 9};
+  const bool staged = w->K.nchunks > 0 && w->KT.nchunks > 0 && staged_setup() == 0;
+  const int unrolls[8] = {1, 2, 4, 0, 8, 9, 16, 17};
   const int bps[5] = {2, 3, 4, 6, 8};
   // UCPDHG_TUNE_LOG=1 prints every timed candidate to stderr
   const char* log_env = std::getenv("UCPDHG_TUNE_LOG");
@@ -196,8 +205,9 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
     const int nsl = which == 0 ? w->K.nslices : w->KT.nslices;
     float best = 1e30f;
     int bu = 1, bg = which == 0 ? w->grid_k : w->grid_kt;
-    for (int ui = 0; ui < 6; ++ui) {
+    for (int ui = 0; ui < 8; ++ui) {
       const int U = unrolls[ui];
+      if (U >= 16 && !staged) continue;
       const int Us = (U == 2 || U == 4) ? U : 1;
       const int need = (nsl + kWarps * Us - 1) / (kWarps * Us);
       for (int bi = 0; bi < 5; ++bi) {
@@ -305,8 +315,8 @@ static int validate_opts(const pdhg_opts* o) {
     return fail(PDHG_ERR_INVALID_ARG, "opts: fixed_eta needs fixed_omega > 0");
   if (!(o->kernel_variant == -1 || o->kernel_variant == 0 || o->kernel_variant == 1 ||
         o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 8 ||
-        o->kernel_variant == 9))
-    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8 or 9");
+        o->kernel_variant == 9 || o->kernel_variant == 16 || o->kernel_variant == 17))
+    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8, 9, 16 or 17");
   if (o->ir_fold_checks < 0)
     return fail(PDHG_ERR_INVALID_ARG, "opts: ir_fold_checks must be >= 0");
   if (!(o->infeas_tol >= 0.0))
@@ -469,6 +479,8 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     const DevState& h = *w->st_host;
+    if (h.wait_timeout)
+      return fail(PDHG_ERR_TIMEOUT, "a staged per-attempt kernel's bounded wait for its bulk copy gave up");
     k_done += h.k;
     accepted += h.accepted;
     restarts += h.restarts;
@@ -629,6 +641,13 @@ extern "C" int pdhg_workspace_create(const pdhg_problem* prob, const pdhg_opts* 
   w->KT.nslices = (int32_t)(L.t_off.size() - 1);
   w->KT.rows = (int32_t)w->n;
   w->KT.nnz_pad = L.t_col.size();
+  std::vector<int32_t> kch, tch;
+  if (build_chunks(L.k_off, &kch) && build_chunks(L.t_off, &tch)) {
+    w->K.nchunks = (int32_t)kch.size() - 1;
+    w->KT.nchunks = (int32_t)tch.size() - 1;
+    if (up(&w->K.chunks, kch) || up(&w->KT.chunks, tch))
+      return bail(fail(PDHG_ERR_NOMEM, "device allocation/upload of the chunk tables failed"));
+  }
   if (up(&w->perm_row, L.perm_row) || up(&w->perm_col, L.perm_col) || up(&w->K.off, L.k_off) ||
       up(&w->K.col, L.k_col) || up(&w->K.src, L.k_src) || up(&w->KT.off, L.t_off) ||
       up(&w->KT.col, L.t_col) || up(&w->KT.src, L.t_src))

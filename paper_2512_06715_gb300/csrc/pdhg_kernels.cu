@@ -116,53 +116,6 @@ __device__ __forceinline__ T sell_dot(const SellView<T>& A, int s, int lane, con
   return acc[0];
 }
 
-// Adaptive step rule on the device (thread 0 of the last block of k_dual).
-template <class T>
-__device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, double inter) {
-  const double eta = st->eta, omega = st->omega;
-  const double movement = omega * st->dx2 + dy2 / omega;
-  const double interaction = 2.0 * fabs(inter);
-  const double eta_max = interaction > 0.0 ? movement / interaction : INFINITY;
-  const int64_t k = st->k + 1;
-  st->k = k;
-  // attempts of all rounds: a refinement round is a change of coordinates,
-  // not a new solve
-  const int64_t kg = st->k_offset + k;
-  double eta_next = fmin((1.0 - step_power(kg + 1, st->red_exp)) * eta_max,
-                         (1.0 + step_power(kg + 1, st->grow_exp)) * eta);
-  if (sizeof(T) == 4) eta_next = fmin(eta_next, fp32_step_cap(omega));
-  int accept = eta <= eta_max;
-  if (st->fixed) {
-    accept = 1;
-    eta_next = eta;
-  }
-  if (st->trace_on && a.trace_a) {
-    int64_t t = st->n_trace_a;
-    if (t < st->trace_cap_a) {
-      double* r = a.trace_a + t * 5;
-      r[0] = eta;
-      r[1] = omega;
-      r[2] = (double)accept;
-      r[3] = eta_max;
-      r[4] = eta_next;
-    }
-    st->n_trace_a = t + 1;
-  }
-  if (accept) {
-    st->par = 1 - st->par;
-    st->w_last = eta;
-    st->pending_w = eta;
-    st->wsum += eta;
-    st->accepted += 1;
-  } else {
-    st->w_last = 0.0;
-    st->pending_w = 0.0;
-  }
-  st->accepted_last = accept;
-  st->since_restart += 1;
-  st->eta = eta_next;
-}
-
 template <class T, int U, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_dual(IterArgs<T> a) {
   DevState* st = a.st;
@@ -638,6 +591,7 @@ __global__ void k_state_init(DevState* st, RoundInit r, const double* scalars) {
   st->grow_exp = r.grow_exp;
   st->infeas_eps = r.infeas_eps;
   st->fold_every = r.fold_every;
+  st->wait_timeout = 0;
   st->fixed = r.fixed;
   st->art_total = r.art_total;
   st->trace_on = r.trace_on;
@@ -680,7 +634,9 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
 // Variants: 1, 2, 4 slices per warp; 0 software pipelined; 8 and 9 are the
 // one-slice and the pipelined forms compiled for 8 resident blocks per SM
 // (at most 32 registers, a few spilled to L1) -- more warps in flight against
-// the HBM and L2 latency at the cost of the spills.
+// the HBM and L2 latency at the cost of the spills; 16 and 17 stage the matrix
+// in shared memory with bulk copies (pdhg_staged.cu), one or two slices per
+// warp at a time.
 template <class T>
 void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
@@ -689,6 +645,8 @@ void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
     case 4: k_dual<T, 4, 1><<<grid, kBlock, 0, s>>>(a); break;
     case 8: k_dual<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 9: k_dual_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
+    case 16: launch_dual_staged<T>(a, grid, s, 1); break;
+    case 17: launch_dual_staged<T>(a, grid, s, 2); break;
     default: k_dual<T, 1, 1><<<grid, kBlock, 0, s>>>(a); break;
   }
 }
@@ -701,6 +659,8 @@ void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) 
     case 4: k_adjoint<T, 4, 1><<<grid, kBlock, 0, s>>>(a); break;
     case 8: k_adjoint<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 9: k_adjoint_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
+    case 16: launch_adjoint_staged<T>(a, grid, s, 1); break;
+    case 17: launch_adjoint_staged<T>(a, grid, s, 2); break;
     default: k_adjoint<T, 1, 1><<<grid, kBlock, 0, s>>>(a); break;
   }
 }
