@@ -137,7 +137,9 @@ typedef struct pdhg_opts {
                                is <= infeas_tol x |objective| with the certificate's
                                sign (dual > 0, primal < 0) ends the solve with
                                PDHG_STATUS_PRIMAL_INFEASIBLE / _DUAL_INFEASIBLE.
-                               0 disables; default 1e-8                             */
+                               Rays of FP32 iterates (mixed precision, batched
+                               solves) carry ~1e-7 relative noise and are tested at
+                               max(infeas_tol, 1e-6).  0 disables; default 1e-8     */
   int32_t ir_fold_checks;   /* mixed: a refinement round also ends after this many
                                checks without reaching its target, folding the
                                current iterate into x*, y* all the same, so the FP32
@@ -216,8 +218,9 @@ int pdhg_backward(void *ws, double g_cost, const double *g_x, double *grad_q, do
  * there) -- and, when it is square (as many active rows as free variables),
  * the basic solution of that set is computed in FP64 on the device:
  *   x_B = the bounds,  K_{A,F} x_F = q_A - K_{A,B} x_B,  K_{A,F}^T y_A = c_F,  y = 0 elsewhere
- * (conjugate gradients on the normal equations with the workspace's matrix,
- * relative residual 1e-13, one CUDA graph per system).  x_out [n], y_out [m]:
+ * (Jacobi-preconditioned conjugate gradients on the normal equations with the
+ * workspace's matrix, aiming at relative residual 1e-13, one CUDA graph per
+ * system).  x_out [n], y_out [m]:
  * device, original order, may be NULL; written only when the set is square.
  * *res (host) reports the outcome and the optimality measures of the polished
  * point (same definitions as pdhg_result, plus the l2 norms of its bound
@@ -226,7 +229,7 @@ int pdhg_backward(void *ws, double g_cost, const double *g_x, double *grad_q, do
  * that basis; violations flag a wrongly detected set. */
 #define PDHG_POLISH_OK 1             /* both systems solved                       */
 #define PDHG_POLISH_NOT_SQUARE 2     /* degenerate: active rows != free variables */
-#define PDHG_POLISH_NO_CONVERGENCE 3 /* CG stopped before 1e-13 (singular set?)   */
+#define PDHG_POLISH_NO_CONVERGENCE 3 /* a system stayed above 1e-9 (singular set?)  */
 typedef struct pdhg_polish_result {
   int32_t status;                 /* PDHG_POLISH_*                              */
   int32_t cg_iterations_primal;   /* CG iterations of the two systems           */
@@ -237,6 +240,8 @@ typedef struct pdhg_polish_result {
   double primal_obj, dual_obj;
   double bound_violation;         /* ||max(l - x, 0) + max(x - u, 0)||_2         */
   double dual_sign_violation;     /* ||min(y_i, 0) over >= rows||_2              */
+  double cg_residual_primal;      /* relative residuals of the two systems; OK  */
+  double cg_residual_dual;        /* needs both <= 1e-9                          */
 } pdhg_polish_result;
 
 int pdhg_polish(void *ws, double *x_out, double *y_out, pdhg_polish_result *res, void *stream);

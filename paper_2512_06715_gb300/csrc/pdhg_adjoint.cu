@@ -11,7 +11,8 @@
 //   d (g_x^T x*) / d q_A = lambda_A  with  S^T lambda_A = g_F,  d (g_x^T x*) / d c = 0
 //   polish:  S x_F = q_A - K_{A,B} x_B  (x_B at its bounds),  S^T y_A = c_F
 // In the rescaled space K~ = Dr K Dc these are systems with S~ = K~_{A,F}, solved
-// by conjugate gradients on the normal equations S~ S~^T z = rhs with the FP64
+// by conjugate gradients on the normal equations S~ S~^T z = rhs (Jacobi
+// preconditioned: diag(S~ S~^T)_i = sum over free j of K~_ij^2) with the FP64
 // sliced-ELL products of the workspace under row/column masks:
 //   mode 0 (S~^T z = r):  S~ S~^T z = S~ r, converged when ||S~^T z - r|| <= tol ||r||
 //   mode 1 (S~ x = b):    S~ S~^T z = b, x = S~^T z, converged when ||S~ S~^T z - b|| <= tol ||b||
@@ -40,7 +41,7 @@ int vg(int64_t n) {
 
 // Device-resident CG scalars.
 struct CGState {
-  double rr, rr0, alpha, beta, target, resid;
+  double rr, rr0, alpha, beta, target, resid, rhs2;  // rr: preconditioned r^T M^-1 r
   int64_t it, max_it;
   int32_t mode, done, converged, pad;
   uint32_t counter, counter2;
@@ -133,6 +134,26 @@ __global__ void __launch_bounds__(kBlock) k_mspmv(SellView<double> A, const doub
   }
 }
 
+// Jacobi preconditioner of S~ S~^T: dinv_i = 1 / sum_{j free} K~_ij^2 on active
+// rows (1 elsewhere, where the residual is 0 anyway).
+__global__ void __launch_bounds__(kBlock) k_jacobi(SellView<double> A, const double* __restrict__ colF,
+                                                   const double* __restrict__ rowA, double* dinv) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = gw; s < A.nslices; s += nw) {
+    const int o0 = A.off[s], w = (A.off[s + 1] - o0) >> 5;
+    double d = 0.0;
+    for (int k = 0; k < w; ++k) {
+      const int slot = o0 + k * kSlice + lane;
+      const double v = __ldg(A.val + slot);
+      d += v * v * __ldg(colF + __ldg(A.col + slot));
+    }
+    const int r = s * kSlice + lane;
+    if (r < A.rows) dinv[r] = (rowA[r] > 0.0 && d > 0.0) ? 1.0 / d : 1.0;
+  }
+}
+
 __global__ void k_cg_init(CGState* cg, int mode, double tol2, int64_t max_it) {
   cg->mode = mode;
   cg->target = tol2;  // scaled by ||rhs||^2 in k_cg_start
@@ -144,31 +165,36 @@ __global__ void k_cg_init(CGState* cg, int mode, double tol2, int64_t max_it) {
   cg->counter = cg->counter2 = 0;
 }
 
-// z = 0, P = R; rr = R.R, and ||rhs||^2 (r.r over n in mode 0, R.R in mode 1).
+// z = 0, P = M^-1 R; rr = R^T M^-1 R, and ||rhs||^2 (r.r over n in mode 0,
+// R.R in mode 1).
 __global__ void __launch_bounds__(kBlock) k_cg_start(double* z, double* P, const double* __restrict__ R,
+                                                     const double* __restrict__ dinv,
                                                      const double* __restrict__ r, int64_t m, int64_t n,
                                                      CGState* cg, double* partials) {
   const int mode = cg->mode;
-  double v[2] = {0.0, 0.0};
+  double v[3] = {0.0, 0.0, 0.0};
   const int64_t N = n > m ? n : m;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
     if (t < m) {
       z[t] = 0.0;
-      P[t] = R[t];
-      v[0] += R[t] * R[t];
+      const double zt = dinv[t] * R[t];
+      P[t] = zt;
+      v[0] += R[t] * zt;
+      v[2] += R[t] * R[t];
     }
     if (mode == 0 && t < n) v[1] += r[t] * r[t];
   }
-  if (publish_partials<2>(v, partials, &cg->counter)) {
-    double tot[2];
-    final_sum<2>(partials, gridDim.x, tot);
+  if (publish_partials<3>(v, partials, &cg->counter)) {
+    double tot[3];
+    final_sum<3>(partials, gridDim.x, tot);
     if (threadIdx.x == 0) {
-      const double gg = mode == 0 ? tot[1] : tot[0];
+      const double gg = mode == 0 ? tot[1] : tot[2];
       cg->rr = tot[0];
       cg->rr0 = tot[0];
+      cg->rhs2 = gg;
       cg->target *= (gg > 0.0 ? gg : 1.0);
-      if (!(tot[0] > 0.0)) {
+      if (!(tot[2] > 0.0)) {
         cg->done = 1;
         cg->converged = 1;
       }
@@ -198,10 +224,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_pq(const double* __restrict__ P, 
   }
 }
 
-// z += alpha P, R -= alpha Q; beta = R.R / rr, rr = R.R
+// z += alpha P, R -= alpha Q, Zp = M^-1 R; beta = R^T Zp / rr, rr = R^T Zp
 __global__ void __launch_bounds__(kBlock) k_cg_update(double* z, const double* __restrict__ P, double* R,
-                                                      const double* __restrict__ Q, int64_t m,
-                                                      CGState* cg, double* partials) {
+                                                      const double* __restrict__ Q,
+                                                      const double* __restrict__ dinv, double* Zp,
+                                                      int64_t m, CGState* cg, double* partials) {
   if (cg->done) return;
   const double alpha = cg->alpha;
   double v[1] = {0.0};
@@ -210,7 +237,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(double* z, const double* _
     z[t] += alpha * P[t];
     const double rn = R[t] - alpha * Q[t];
     R[t] = rn;
-    v[0] += rn * rn;
+    const double zn = dinv[t] * rn;
+    Zp[t] = zn;
+    v[0] += rn * zn;
   }
   if (publish_partials<1>(v, partials, &cg->counter)) {
     double tot[1];
@@ -225,13 +254,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(double* z, const double* _
   }
 }
 
-// P = R + beta P
-__global__ void k_cg_dir(double* P, const double* __restrict__ R, int64_t m, const CGState* cg) {
+// P = Zp + beta P  (Zp = M^-1 R)
+__global__ void k_cg_dir(double* P, const double* __restrict__ Zp, int64_t m, const CGState* cg) {
   if (cg->done) return;
   const double beta = cg->beta;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
        t += (int64_t)gridDim.x * blockDim.x)
-    P[t] = R[t] + beta * P[t];
+    P[t] = Zp[t] + beta * P[t];
 }
 
 // True residual: mode 0 ||T - r||^2 over n (T = S^T z), mode 1 ||Q2 - b||^2 over m
@@ -391,7 +420,7 @@ __global__ void k_unscale_out(const int32_t* __restrict__ perm, const double* __
 struct AdjBufs {
   double *Kx = nullptr, *KTy = nullptr, *rowA = nullptr, *colF = nullptr, *xfix = nullptr;
   double *z = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr, *Q2 = nullptr, *b = nullptr;
-  double *T = nullptr, *r = nullptr, *xp = nullptr, *yp = nullptr;
+  double *T = nullptr, *r = nullptr, *xp = nullptr, *yp = nullptr, *dinv = nullptr, *Zp = nullptr;
   CGState* cg = nullptr;
   CGState* cg_host = nullptr;  // pinned
   cudaGraph_t graph = nullptr;
@@ -417,7 +446,8 @@ static int adj_bufs(Workspace* w, AdjBufs** out) {
   }
   AdjBufs* ab = new AdjBufs();
   const int64_t n = w->n, m = w->m;
-  double** vm[] = {&ab->Kx, &ab->rowA, &ab->z, &ab->R, &ab->P, &ab->Q, &ab->Q2, &ab->b, &ab->yp};
+  double** vm[] = {&ab->Kx, &ab->rowA, &ab->z, &ab->R, &ab->P, &ab->Q, &ab->Q2, &ab->b, &ab->yp,
+                   &ab->dinv, &ab->Zp};
   double** vn[] = {&ab->KTy, &ab->colF, &ab->xfix, &ab->T, &ab->r, &ab->xp};
   bool ok = true;
   for (double** p : vm) {
@@ -454,8 +484,8 @@ static void cg_body(Workspace* w, AdjBufs* ab, cudaStream_t s, unsigned long lon
     k_mspmv<<<w->grid_kt, kBlock, 0, s>>>(w->KT.v64(), ab->P, ab->rowA, ab->colF, ab->T, ab->cg, -1);
     k_mspmv<<<w->grid_k, kBlock, 0, s>>>(w->K.v64(), ab->T, ab->colF, ab->rowA, ab->Q, ab->cg, -1);
     k_cg_pq<<<vg(m), kBlock, 0, s>>>(ab->P, ab->Q, m, ab->cg, part);
-    k_cg_update<<<vg(m), kBlock, 0, s>>>(ab->z, ab->P, ab->R, ab->Q, m, ab->cg, part);
-    k_cg_dir<<<vg(m), kBlock, 0, s>>>(ab->P, ab->R, m, ab->cg);
+    k_cg_update<<<vg(m), kBlock, 0, s>>>(ab->z, ab->P, ab->R, ab->Q, ab->dinv, ab->Zp, m, ab->cg, part);
+    k_cg_dir<<<vg(m), kBlock, 0, s>>>(ab->P, ab->Zp, m, ab->cg);
   }
   k_mspmv<<<w->grid_kt, kBlock, 0, s>>>(w->KT.v64(), ab->z, ab->rowA, ab->colF, ab->T, ab->cg, -1);
   k_mspmv<<<w->grid_k, kBlock, 0, s>>>(w->K.v64(), ab->T, ab->colF, ab->rowA, ab->Q2, ab->cg, 1);
@@ -514,7 +544,7 @@ static int cg_run(Workspace* w, AdjBufs* ab, int mode, double tol, int64_t max_i
     k_mspmv<<<w->grid_k, kBlock, 0, s>>>(w->K.v64(), ab->r, ab->colF, ab->rowA, ab->R, nullptr, -1);
   else
     cudaMemcpyAsync(ab->R, ab->b, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
-  k_cg_start<<<vg(n > m ? n : m), kBlock, 0, s>>>(ab->z, ab->P, ab->R, ab->r, m, n, ab->cg,
+  k_cg_start<<<vg(n > m ? n : m), kBlock, 0, s>>>(ab->z, ab->P, ab->R, ab->dinv, ab->r, m, n, ab->cg,
                                                    w->partials);
   cudaError_t e = cudaGraphLaunch(ab->exec, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ab->cg_host, ab->cg, sizeof(CGState), cudaMemcpyDeviceToHost, s);
@@ -538,6 +568,7 @@ static int classify(Workspace* w, AdjBufs* ab, cudaStream_t s, int64_t* nA, int6
   k_classify<<<gN, kBlock, 0, s>>>(w->x_star, w->y_star, ab->Kx, ab->KTy, w->q_s, w->c_s, w->l_s, w->u_s,
                                    n, m, w->m_eq, ab->rowA, ab->colF, ab->xfix, w->partials);
   k_final2<<<1, kBlock, 0, s>>>(w->partials, gN, scal);
+  k_jacobi<<<w->grid_k, kBlock, 0, s>>>(w->K.v64(), ab->colF, ab->rowA, ab->dinv);
   double hs[2];
   if (cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
@@ -550,6 +581,11 @@ static int classify(Workspace* w, AdjBufs* ab, cudaStream_t s, int64_t* nA, int6
 }
 
 static int64_t cg_max_it(int64_t nA) { return std::min<int64_t>(20 * (nA + 10), 200000); }
+
+// A polish is accepted when both systems reach this relative residual (the CG
+// aims at 1e-13; the normal equations square the active set's condition number,
+// which can stop FP64 CG short of that).
+constexpr double kPolishAccept = 1e-9;
 
 }  // namespace ucpdhg
 
@@ -674,6 +710,11 @@ extern "C" int pdhg_polish(void* ws, double* x_out, double* y_out, pdhg_polish_r
   res->dual_sign_violation = std::sqrt(h[6]);
   res->cg_iterations_primal = (int32_t)sp.it;
   res->cg_iterations_dual = (int32_t)sd.it;
-  res->status = (sp.converged && sd.converged) ? PDHG_POLISH_OK : PDHG_POLISH_NO_CONVERGENCE;
+  // relative residuals of the two systems at their last true-residual check
+  res->cg_residual_primal = sp.converged && sp.resid == 0.0 ? 0.0 : std::sqrt(sp.resid / std::max(sp.rhs2, 1e-300));
+  res->cg_residual_dual = sd.converged && sd.resid == 0.0 ? 0.0 : std::sqrt(sd.resid / std::max(sd.rhs2, 1e-300));
+  res->status = (std::max(res->cg_residual_primal, res->cg_residual_dual) <= kPolishAccept)
+                    ? PDHG_POLISH_OK
+                    : PDHG_POLISH_NO_CONVERGENCE;
   return PDHG_OK;
 }

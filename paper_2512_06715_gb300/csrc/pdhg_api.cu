@@ -443,7 +443,7 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
       ri.omega_smooth = o.omega_smoothing;
       ri.red_exp = o.step_reduction_exp;
       ri.grow_exp = o.step_growth_exp;
-      ri.infeas_eps = o.infeas_tol;
+      ri.infeas_eps = (mixed && o.infeas_tol > 0.0) ? std::max(o.infeas_tol, kFp32RayTol) : o.infeas_tol;
       ri.fold_every = o.ir_fold_checks;
       if (r == 0 && !w->tune[mixed ? 1 : 0].done) {
         launch_state_init(w->st, ri, w->scalars, s);

@@ -1279,7 +1279,7 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   gin.grow_exp = o.step_growth_exp;
   gin.max_k = o.max_iters;
   gin.t_limit_ns = (uint64_t)(o.time_limit_s * 1e9);
-  gin.infeas_eps = o.infeas_tol;
+  gin.infeas_eps = o.infeas_tol > 0.0 ? std::max(o.infeas_tol, kFp32RayTol) : 0.0;  // FP32 iterates
   gin.fold_every = o.ir_fold_checks;
   gin.n_real = B;
   kb_init_state<<<1, BP < 32 ? 32 : BP, 0, s>>>(bt->inst, bt->g, B, BP, w->scalars, gin);

@@ -64,7 +64,8 @@ class pdhg_polish_result(C.Structure):
                 ("active_rows", C.c_int64), ("free_vars", C.c_int64),
                 ("rel_p", C.c_double), ("rel_d", C.c_double), ("rel_gap", C.c_double),
                 ("rel_kkt", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
-                ("bound_violation", C.c_double), ("dual_sign_violation", C.c_double)]
+                ("bound_violation", C.c_double), ("dual_sign_violation", C.c_double),
+                ("cg_residual_primal", C.c_double), ("cg_residual_dual", C.c_double)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

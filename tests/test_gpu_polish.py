@@ -46,20 +46,23 @@ def test_polish_gives_the_vertex(case):
     xp, yp, res = ws.polish()
     assert res["status_name"] == "ok", res
     assert res["active_rows"] == res["free_vars"]
+    assert max(res["cg_residual_primal"], res["cg_residual_dual"]) <= 1e-9
     xp, yp = xp.cpu().numpy(), yp.cpu().numpy()
-    # the HiGHS vertex, to solver accuracy
-    assert np.abs(xp - xh).max() <= 1e-9 * np.abs(xh).max()
-    assert np.abs(yp - yh).max() <= 1e-8 * np.abs(yh).max()
-    assert abs(res["primal_obj"] - obj) <= 1e-12 * abs(obj)
+    # the HiGHS vertex (the iterative solves stop at relative residual <= 1e-9)
+    assert np.abs(xp - xh).max() <= 1e-7 * np.abs(xh).max()
+    assert np.abs(yp - yh).max() <= 1e-6 * np.abs(yh).max()
+    assert abs(res["primal_obj"] - obj) <= 1e-9 * abs(obj)
     # the library's measures of the polished point equal the oracle's
     chk = kkt(lp, xp, yp)
-    assert chk.rel_kkt <= 1e-12 and res["rel_kkt"] <= 1e-12
-    assert res["bound_violation"] <= 1e-9 and res["dual_sign_violation"] <= 1e-9
+    assert chk.rel_kkt <= 1e-9 and res["rel_kkt"] <= 1e-9
+    assert abs(chk.rel_kkt - res["rel_kkt"]) <= 1e-3 * chk.rel_kkt + 1e-15
+    assert res["bound_violation"] <= 1e-7 * np.abs(xh).max()
+    assert res["dual_sign_violation"] <= 1e-6 * np.abs(yh).max()
     # the oracle's polish of the same GPU point (same active set, direct solver)
     ref = polish(lp, x, y)
     assert ref is not None
-    assert np.abs(xp - ref[0]).max() <= 1e-10 * np.abs(ref[0]).max()
-    assert np.abs(yp - ref[1]).max() <= 1e-9 * np.abs(ref[1]).max()
+    assert np.abs(xp - ref[0]).max() <= 1e-7 * np.abs(ref[0]).max()
+    assert np.abs(yp - ref[1]).max() <= 1e-6 * np.abs(ref[1]).max()
 
 
 def test_polish_reports_a_degenerate_set():
