@@ -14,7 +14,11 @@ pdhg_solve_batched, up to 64 nodes per call; the host keeps the tree.
 * branching on the most fractional commitment, children u = 0 and u = 1;
 * incumbents: a node whose commitments come out integral (within int_tol),
   and the rounding heuristic at every solved node (every fractional u rounded
-  up, the LP with all commitments fixed solved in the same batch machinery).
+  up, the LP with all commitments fixed solved in the same batch machinery);
+* a node the batched FP32 solve leaves unresolved (attempt or time limit: the
+  FP32 rays of some infeasible nodes never certify) is solved again alone in
+  FP64 by pdhg_solve with the node's bounds; if that also ends unresolved the
+  driver raises rather than guess.
 The tree, the queue and the decisions are host logic; no method arithmetic runs
 here beyond comparing the objectives the library returns.
 """
@@ -47,12 +51,31 @@ class BnBResult:
     log: list = field(default_factory=list)
 
 
+def _solve_alone_fp64(ws, l, u, max_iters):
+    """One node LP in FP64 (pdhg_solve) on the workspace's own bounds, which are
+    restored afterwards; returns (x, result dict)."""
+    import torch
+    keep = {k: ws.t[k].clone() for k in ("l", "u")}
+    saved = {k: getattr(ws.opts, k) for k in ("precision", "max_iters")}
+    try:
+        ws.t["l"].copy_(torch.as_tensor(l, device=ws.device))
+        ws.t["u"].copy_(torch.as_tensor(u, device=ws.device))
+        ws.set_opts(precision="fp64", max_iters=max_iters)
+        x, _, r = ws.solve()
+        return x.cpu().numpy(), r
+    finally:
+        for k, v in keep.items():
+            ws.t[k].copy_(v)
+        ws.set_opts(**saved)
+
+
 def branch_and_bound(ws, idx_u: np.ndarray, l0: np.ndarray, u0: np.ndarray, batch: int = 64,
                      max_nodes: int = 2000, gap: float = 1e-6, int_tol: float = 1e-6,
-                     device=None) -> BnBResult:
-    """B&B on the UC MILP whose relaxation `ws` (a pdhg.Workspace, mixed or FP64
-    options set by the caller) holds; idx_u [T, G] are the commitment
-    variables, l0, u0 the relaxation's bounds (original order)."""
+                     fp64_retry_iters: int = 10_000_000, device=None) -> BnBResult:
+    """B&B on the UC MILP whose relaxation `ws` (a pdhg.Workspace whose options
+    -- tolerance, attempt and time limits of each batched call -- the caller
+    sets) holds; idx_u [T, G] are the commitment variables, l0, u0 the
+    relaxation's bounds (original order)."""
     import torch
 
     dev = device if device is not None else ws.device
@@ -61,7 +84,7 @@ def branch_and_bound(ws, idx_u: np.ndarray, l0: np.ndarray, u0: np.ndarray, batc
     pruned_inf = pruned_bound = 0
     seq = 0
     open_nodes: list[_Node] = [_Node(-np.inf, seq, {}, 0)]
-    solved = batches = 0
+    solved = batches = retried = 0
     log = []
 
     def bounds_of(fix: dict):
@@ -97,6 +120,10 @@ def branch_and_bound(ws, idx_u: np.ndarray, l0: np.ndarray, u0: np.ndarray, batc
         rounded = []
         for k, (kind, nd) in enumerate(kinds):
             r = res[k]
+            if r["status_name"] in ("iteration_limit", "time_limit"):
+                xk, r = _solve_alone_fp64(ws, ls[k], us[k], fp64_retry_iters)
+                x_b[k] = xk
+                retried += 1
             if r["status_name"] == "primal_infeasible":
                 pruned_inf += 1
                 continue
@@ -132,7 +159,7 @@ def branch_and_bound(ws, idx_u: np.ndarray, l0: np.ndarray, u0: np.ndarray, batc
                     sched = np.array([f[int(j)] for j in flat_u]).reshape(idx_u.shape)
         best_open = min((nd.bound for nd in open_nodes), default=np.inf)
         log.append({"batch": batches, "solved": solved, "open": len(open_nodes), "incumbent": incumbent,
-                    "bound": best_open})
+                    "bound": best_open, "fp64_retries": retried})
     best_open = min((nd.bound for nd in open_nodes
                      if nd.bound < incumbent - gap * max(1.0, abs(incumbent))), default=np.inf)
     bound = min(best_open, incumbent)

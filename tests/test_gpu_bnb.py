@@ -36,7 +36,10 @@ def test_bnb_reaches_the_enumerated_milp_optimum(shape, seed):
             best = json.load(f)["milp_optimum"]
     else:
         best, _ = milp_by_enumeration(lp, inst.idx_u)
-    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=1e-9, time_limit_s=120.0))
+    # each batched call capped at 200k attempts per node; a node left unresolved
+    # is solved again alone in FP64
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=1e-9, max_iters=200_000,
+                                                    time_limit_s=120.0))
     res = branch_and_bound(ws, inst.idx_u, inst.l, inst.u, gap=1e-7)
     ws.close()
     assert res.status == "optimal", res
