@@ -278,6 +278,7 @@ def node_throughput(args, dev, stream, pdhg, world=1, rank=0):
 
     local = []
     tb = 0.0
+    tuning = None
     if stop > start:
         l_b = torch.as_tensor(l_np[start:stop], device=dev)
         u_b = torch.as_tensor(u_np[start:stop], device=dev)
@@ -285,6 +286,7 @@ def node_throughput(args, dev, stream, pdhg, world=1, rank=0):
         if not converged:
             wb.solve_batched(l_b, u_b, want_y=False)  # allocations, graph
         tb, (_, _, rb) = event_time(lambda: wb.solve_batched(l_b, u_b, want_y=False))
+        tuning = wb.tuning()["batched"]
         wb.close()
         local = [{"node": start + k, "status": r["status_name"], "attempts": r["iterations"],
                   "rel_kkt": r["rel_kkt"], "ir_rounds": r["ir_rounds"]} for k, r in enumerate(rb)]
@@ -305,7 +307,8 @@ def node_throughput(args, dev, stream, pdhg, world=1, rank=0):
             att_seq.append(r1["iterations"])
     total_att = sum(n["attempts"] for n in nodes)
     out = {"workload": args.nodes_workload, "n": inst.n, "m": inst.m, "nnz": inst.nnz, "nodes": B,
-           "ranks": world, "partition": [list(node_partition(B, world, r)) for r in range(world)]}
+           "ranks": world, "partition": [list(node_partition(B, world, r)) for r in range(world)],
+           "batched_tuning": tuning}
     if converged:
         att = np.array([n["attempts"] for n in nodes])
         statuses = sorted({n["status"] for n in nodes})

@@ -301,8 +301,10 @@ int pdhg_apply_K(void *ws, int32_t transpose, int32_t precision, const double *i
 int pdhg_get_trace(void *ws, double *attempts, int64_t cap_a, double *checks, int64_t cap_c,
                    int64_t *n_a, int64_t *n_c);
 
-/* Launch configuration chosen for the per-attempt kernels, host int32 [8]:
- * FP64 {dual unroll, dual grid, adjoint unroll, adjoint grid}, then FP32.
+/* Launch configuration chosen for the per-attempt kernels, host int32 [12]:
+ * FP64 {dual unroll, dual grid, adjoint unroll, adjoint grid}, then FP32, then
+ * the batched sweeps {dual rows per warp, dual grid, adjoint columns per warp,
+ * adjoint grid} (-1 and 0 before the first batched solve).
  * unroll 1, 2, 4: 32-row slices a warp sweeps together; 0: one slice per warp,
  * software pipelined (the next slice's first entries and row operands are
  * loaded while the current slice's gathers are in flight); 8, 9: variants 1

@@ -180,6 +180,8 @@ IterArgs<T> make_args(Workspace* w);
 
 // pdhg_batched.cu: frees the batched buffers and graph of a workspace
 void release_batched(Workspace* w);
+// pdhg_batched.cu: rows per warp and grid of the batched sweeps (dual, adjoint)
+void batched_tuning(Workspace* w, int32_t* out4);
 // pdhg_adjoint.cu: frees the adjoint's scratch
 void release_adjoint(Workspace* w);
 

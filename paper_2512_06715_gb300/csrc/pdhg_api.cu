@@ -850,6 +850,7 @@ extern "C" int pdhg_get_tuning(void* ws, int32_t* cfg) {
     cfg[4 * p + 2] = t.done ? t.unroll_adj : -1;
     cfg[4 * p + 3] = t.done ? t.grid_adj : 0;
   }
+  batched_tuning(w, cfg + 8);
   return PDHG_OK;
 }
 

@@ -20,6 +20,8 @@
 // step size, primal weight and restart window carry over.  The whole batch is
 // one CUDA graph whose while loop runs until every instance is done.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -35,8 +37,27 @@ constexpr int kKktWarps = 4;          // smaller blocks for the FP64 check sweep
 constexpr int kApplyRows = 4;         // rows per block of the elementwise kernels (x BP threads)
 constexpr int kRowS = 7, kColS = 9;   // per-candidate sums (as in the single-instance check,
                                       // including the infeasibility-ray sums)
-constexpr int kRowsPerWarp = 4;       // rows (columns) a warp sweeps together in kb_dual (kb_adjoint)
-static_assert(kRowsPerWarp == 4 && kSlice % kRowsPerWarp == 0, "int4/float4 entry loads");
+// Rows (columns) a warp sweeps together in kb_dual (kb_adjoint): R = 4, 2 or 1
+// adjacent slots of a slice, read as int4/float4, int2/float2 or scalars; the
+// batched autotuner picks R and the grid per matrix and batch width.
+template <int R>
+__device__ __forceinline__ void load_slots(const int32_t* __restrict__ c, const float* __restrict__ v,
+                                           int (&cc)[R], float (&vv)[R]) {
+  if constexpr (R == 4) {
+    const int4 c4 = __ldg(reinterpret_cast<const int4*>(c));
+    const float4 v4 = __ldg(reinterpret_cast<const float4*>(v));
+    cc[0] = c4.x; cc[1] = c4.y; cc[2] = c4.z; cc[3] = c4.w;
+    vv[0] = v4.x; vv[1] = v4.y; vv[2] = v4.z; vv[3] = v4.w;
+  } else if constexpr (R == 2) {
+    const int2 c2 = __ldg(reinterpret_cast<const int2*>(c));
+    const float2 v2 = __ldg(reinterpret_cast<const float2*>(v));
+    cc[0] = c2.x; cc[1] = c2.y;
+    vv[0] = v2.x; vv[1] = v2.y;
+  } else {
+    cc[0] = __ldg(c);
+    vv[0] = __ldg(v);
+  }
+}
 
 // Per-instance state (array of B structs in device memory).
 struct BInst {
@@ -171,7 +192,7 @@ __device__ __forceinline__ bool last_block(uint32_t* counter) {
 
 // K x' and the projected dual step for every active instance; the last block
 // takes each instance's adaptive step decision.
-template <int BP>
+template <int BP, int RW>
 __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
   BGlobal* g = a.g;
   if (g->all_done) return;
@@ -199,19 +220,19 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
     const int b = lane + 32 * h;
     xg[h] = s_act[b] ? a.x[1 - s_par[b]] + b : nullptr;
   }
-  const int nq = (a.m + kRowsPerWarp - 1) / kRowsPerWarp;
+  const int nq = (a.m + RW - 1) / RW;
   for (int qd = gw; qd < nq; qd += nw) {
-    const int i0 = qd * kRowsPerWarp;  // kRowsPerWarp consecutive rows of one slice
+    const int i0 = qd * RW;  // RW consecutive rows of one slice
     const int s = i0 >> 5;
     const int o_s = __ldg(a.K.off + s);
     const int base = o_s + (i0 & 31);
     const int w = (__ldg(a.K.off + s + 1) - o_s) >> 5;
     // row operands do not depend on the products: issue them first so their
     // latency overlaps the matrix stream and the gathers
-    float ko[kRowsPerWarp][H], yo[kRowsPerWarp][H], qv[kRowsPerWarp][H], lo[kRowsPerWarp][H],
-        yb[kRowsPerWarp][H];
+    float ko[RW][H], yo[RW][H], qv[RW][H], lo[RW][H],
+        yb[RW][H];
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r)
+    for (int r = 0; r < RW; ++r)
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int b = lane + 32 * h, i = i0 + r;
@@ -226,27 +247,26 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
           if (s_pw[b] != 0.f) yb[r][h] = a.ybar[idx];
         }
       }
-    float acc[kRowsPerWarp][H];
+    float acc[RW][H];
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r)
+    for (int r = 0; r < RW; ++r)
 #pragma unroll
       for (int h = 0; h < H; ++h) acc[r][h] = 0.f;
-    // entry k of the group's rows: kRowsPerWarp adjacent slots (16 B aligned:
-    // slice offsets are multiples of 32 and i0 of kRowsPerWarp)
+    // entry k of the group's rows: RW adjacent slots (16 B aligned:
+    // slice offsets are multiples of 32 and i0 of RW)
 #pragma unroll 2
     for (int k = 0; k < w; ++k) {
-      const int4 c4 = __ldg(reinterpret_cast<const int4*>(a.K.col + base + k * kSlice));
-      const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.K.val + base + k * kSlice));
-      const int c[4] = {c4.x, c4.y, c4.z, c4.w};
-      const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+      int c[RW];
+      float v[RW];
+      load_slots<RW>(a.K.col + base + k * kSlice, a.K.val + base + k * kSlice, c, v);
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r)
+      for (int r = 0; r < RW; ++r)
 #pragma unroll
         for (int h = 0; h < H; ++h)
           if (xg[h]) acc[r][h] += v[r] * __ldg(xg[h] + (size_t)c[r] * BP);
     }
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r) {
+    for (int r = 0; r < RW; ++r) {
       const int i = i0 + r;
       if (i >= a.m) continue;
 #pragma unroll
@@ -317,7 +337,7 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
 
 // K^T y' for instances whose step was accepted, the x-average update and the
 // next primal step x'' = proj(x - tau (c - K^T y)).
-template <int BP>
+template <int BP, int RW>
 __global__ void __launch_bounds__(kBThreads) kb_adjoint(BArgs<BP> a) {
   BGlobal* g = a.g;
   if (g->all_done) return;
@@ -346,17 +366,17 @@ __global__ void __launch_bounds__(kBThreads) kb_adjoint(BArgs<BP> a) {
     const int b = lane + 32 * h;
     yg[h] = s_acc[b] ? a.y[s_par[b]] + b : nullptr;
   }
-  const int nq = (a.n + kRowsPerWarp - 1) / kRowsPerWarp;
+  const int nq = (a.n + RW - 1) / RW;
   for (int qd = gw; qd < nq; qd += nw) {
-    const int j0 = qd * kRowsPerWarp;  // kRowsPerWarp consecutive columns of one slice
+    const int j0 = qd * RW;  // RW consecutive columns of one slice
     const int s = j0 >> 5;
     const int o_s = __ldg(a.KT.off + s);
     const int base = o_s + (j0 & 31);
     const int w = (__ldg(a.KT.off + s + 1) - o_s) >> 5;
-    float x0[kRowsPerWarp][H], cv[kRowsPerWarp][H], lv[kRowsPerWarp][H], uv[kRowsPerWarp][H],
-        xb[kRowsPerWarp][H], go[kRowsPerWarp][H];
+    float x0[RW][H], cv[RW][H], lv[RW][H], uv[RW][H],
+        xb[RW][H], go[RW][H];
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r)
+    for (int r = 0; r < RW; ++r)
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int b = lane + 32 * h, j = j0 + r;
@@ -372,25 +392,24 @@ __global__ void __launch_bounds__(kBThreads) kb_adjoint(BArgs<BP> a) {
           if (s_acc[b] && s_wl[b] != 0.f) xb[r][h] = a.xbar[idx];
         }
       }
-    float acc[kRowsPerWarp][H];
+    float acc[RW][H];
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r)
+    for (int r = 0; r < RW; ++r)
 #pragma unroll
       for (int h = 0; h < H; ++h) acc[r][h] = 0.f;
 #pragma unroll 2
     for (int k = 0; k < w; ++k) {
-      const int4 c4 = __ldg(reinterpret_cast<const int4*>(a.KT.col + base + k * kSlice));
-      const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.KT.val + base + k * kSlice));
-      const int c[4] = {c4.x, c4.y, c4.z, c4.w};
-      const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+      int c[RW];
+      float v[RW];
+      load_slots<RW>(a.KT.col + base + k * kSlice, a.KT.val + base + k * kSlice, c, v);
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r)
+      for (int r = 0; r < RW; ++r)
 #pragma unroll
         for (int h = 0; h < H; ++h)
           if (yg[h]) acc[r][h] += v[r] * __ldg(yg[h] + (size_t)c[r] * BP);
     }
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r) {
+    for (int r = 0; r < RW; ++r) {
       const int j = j0 + r;
       if (j >= a.n) continue;
 #pragma unroll
@@ -1104,7 +1123,29 @@ struct Batched {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   int grid_rows = 0, grid_cols = 0, grid_kr = 0, grid_kc = 0, grid_apply = 0;
+  int rw_dual = 4, rw_adj = 4;  // rows (columns) per warp of the sweeps
+  bool tuned = false;
 };
+
+template <int BP>
+void launch_sweep_dual(const BArgs<BP>& a, int rw, int grid, cudaStream_t s) {
+  if (rw == 1)
+    kb_dual<BP, 1><<<grid, kBThreads, 0, s>>>(a);
+  else if (rw == 2)
+    kb_dual<BP, 2><<<grid, kBThreads, 0, s>>>(a);
+  else
+    kb_dual<BP, 4><<<grid, kBThreads, 0, s>>>(a);
+}
+
+template <int BP>
+void launch_sweep_adjoint(const BArgs<BP>& a, int rw, int grid, cudaStream_t s) {
+  if (rw == 1)
+    kb_adjoint<BP, 1><<<grid, kBThreads, 0, s>>>(a);
+  else if (rw == 2)
+    kb_adjoint<BP, 2><<<grid, kBThreads, 0, s>>>(a);
+  else
+    kb_adjoint<BP, 4><<<grid, kBThreads, 0, s>>>(a);
+}
 
 template <class P>
 cudaError_t balloc(Batched* bt, P** p, size_t count) {
@@ -1170,8 +1211,8 @@ int setup_batched(Workspace* w, Batched* bt, BArgs<BP>* out) {
   // stay few (their final sums sit on the critical path of every attempt)
   // the sweeps are grid-stride loops: one wave of resident blocks
   int occ_d = 0, occ_a = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, kb_dual<BP>, kBThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, kb_adjoint<BP>, kBThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, kb_dual<BP, 4>, kBThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, kb_adjoint<BP, 4>, kBThreads, 0);
   occ_d = std::max(occ_d, 1);
   occ_a = std::max(occ_a, 1);
   bt->grid_rows = std::max(1, std::min(sms * occ_d, (int)((w->m + 8 * kBWarps - 1) / (8 * kBWarps))));
@@ -1192,8 +1233,8 @@ template <int BP>
 void launch_body(const BArgs<BP>& a, Batched* bt, cudaStream_t s, int init) {
   if (!init) {
     for (int k = 0; k < kCheckEvery; ++k) {
-      kb_dual<BP><<<bt->grid_rows, kBThreads, 0, s>>>(a);
-      kb_adjoint<BP><<<bt->grid_cols, kBThreads, 0, s>>>(a);
+      launch_sweep_dual<BP>(a, bt->rw_dual, bt->grid_rows, s);
+      launch_sweep_adjoint<BP>(a, bt->rw_adj, bt->grid_cols, s);
     }
   }
   kb_kkt_row<BP><<<bt->grid_kr, kKktWarps * 32, 0, s>>>(a, init);
@@ -1241,33 +1282,12 @@ int build_batched_graph(Workspace* w, Batched* bt, BArgs<BP> a) {
   return PDHG_OK;
 }
 
+// Device state, round-0 data, first primal step and initial KKT_w of every
+// instance.
 template <int BP>
-int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b, double* x_out,
-                       double* y_out, pdhg_result* res, cudaStream_t s) {
-  Batched* bt = (Batched*)w->batched;
-  if (bt && bt->BP != BP) return -99;  // caller rebuilds
-  if (!bt) {
-    bt = new Batched();
-    bt->BP = BP;
-    w->batched = bt;
-    BArgs<BP> a;
-    int rc = setup_batched<BP>(w, bt, &a);
-    if (rc != PDHG_OK) return rc;
-    bt->args = new BArgs<BP>(a);
-  }
-  BArgs<BP> a = *(BArgs<BP>*)bt->args;
-  a.B = B;
-  a.in_graph = 0;
+void batched_start(Workspace* w, Batched* bt, const BArgs<BP>& a, int B, const double* l_b,
+                   const double* u_b, cudaStream_t s) {
   const pdhg_opts& o = w->opts;
-  if (!o.host_loop) {
-    int rc = build_batched_graph<BP>(w, bt, a);
-    if (rc != PDHG_OK) return rc;
-  }
-  cudaEventRecord(w->ev[0], s);
-  launch_prepare(w, s);
-  launch_to_f32(w->K.val64, w->K.val32, w->K.nnz_pad, s);
-  launch_to_f32(w->KT.val64, w->KT.val32, w->KT.nnz_pad, s);
-  w->values_f32 = true;
   BGlobal gin{};
   gin.tol = o.tol;
   gin.red = o.ir_reduction;
@@ -1289,6 +1309,114 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
   kb_first_primal<BP><<<gv, 256, 0, s>>>(a);
   kb_dx2<BP><<<BP, kBlock, 0, s>>>(a);
   launch_body<BP>(a, bt, s, 1);  // initial KKT_w of every instance
+}
+
+// The batched autotuner: rows (columns) per warp R in {1, 2, 4} and the grid
+// (1 to 4 blocks per SM, capped by occupancy and by 8 rows per warp) of each
+// sweep, timed with CUDA events on this matrix and batch width.  UCPDHG_TUNE_LOG=1
+// prints the table to stderr.
+template <int BP>
+int autotune_batched(Workspace* w, Batched* bt, const BArgs<BP>& a, int B, const double* l_b,
+                     const double* u_b, cudaStream_t s) {
+  bt->tuned = true;
+  if (!w->opts.autotune) return PDHG_OK;
+  const char* log_env = std::getenv("UCPDHG_TUNE_LOG");
+  const bool log = log_env && log_env[0] == '1';
+  batched_start<BP>(w, bt, a, B, l_b, u_b, s);
+  const int sms = w->num_sms;
+  for (int which = 0; which < 2; ++which) {
+    const int64_t len = which == 0 ? w->m : w->n;
+    float best = 1e30f;
+    int best_rw = 4, best_grid = which == 0 ? bt->grid_rows : bt->grid_cols;
+    for (int rw : {4, 2, 1}) {
+      int occ = 0;
+      if (which == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, rw == 4 ? (const void*)kb_dual<BP, 4> : rw == 2 ? (const void*)kb_dual<BP, 2> : (const void*)kb_dual<BP, 1>,
+            kBThreads, 0);
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, rw == 4 ? (const void*)kb_adjoint<BP, 4> : rw == 2 ? (const void*)kb_adjoint<BP, 2> : (const void*)kb_adjoint<BP, 1>,
+            kBThreads, 0);
+      occ = std::max(occ, 1);
+      const int need = (int)std::max<int64_t>(1, (len + 8 * kBWarps - 1) / (8 * kBWarps));
+      for (int bps = 1; bps <= std::min(occ, 4); ++bps) {
+        const int g = std::min(std::min(sms * bps, need), 8192);
+        auto run = [&]() {
+          if (which == 0)
+            launch_sweep_dual<BP>(a, rw, g, s);
+          else
+            launch_sweep_adjoint<BP>(a, rw, g, s);
+        };
+        run();
+        cudaEventRecord(w->ev[2], s);
+        for (int r = 0; r < 3; ++r) run();
+        cudaEventRecord(w->ev[3], s);
+        if (cudaEventSynchronize(w->ev[3]) != cudaSuccess) {
+          g_err = std::string("batched autotune: ") + cudaGetErrorString(cudaGetLastError());
+          return PDHG_ERR_CUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, w->ev[2], w->ev[3]);
+        if (log)
+          std::fprintf(stderr, "autotune batched B=%d %s rows/warp %d grid %d: %.2f us\n", B,
+                       which == 0 ? "dual" : "adjoint", rw, g, ms * 1000.f / 3.f);
+        if (ms < best * 0.98f) {
+          best = ms;
+          best_rw = rw;
+          best_grid = g;
+        }
+        if (g == need) break;
+      }
+    }
+    if (which == 0) {
+      bt->rw_dual = best_rw;
+      bt->grid_rows = best_grid;
+    } else {
+      bt->rw_adj = best_rw;
+      bt->grid_cols = best_grid;
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? PDHG_OK : PDHG_ERR_CUDA;
+}
+
+template <int BP>
+int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b, double* x_out,
+                       double* y_out, pdhg_result* res, cudaStream_t s) {
+  Batched* bt = (Batched*)w->batched;
+  if (bt && bt->BP != BP) return -99;  // caller rebuilds
+  if (!bt) {
+    bt = new Batched();
+    bt->BP = BP;
+    w->batched = bt;
+    BArgs<BP> a;
+    int rc = setup_batched<BP>(w, bt, &a);
+    if (rc != PDHG_OK) return rc;
+    bt->args = new BArgs<BP>(a);
+  }
+  BArgs<BP> a = *(BArgs<BP>*)bt->args;
+  a.B = B;
+  a.in_graph = 0;
+  const pdhg_opts& o = w->opts;
+  if (!bt->tuned) {
+    // time the sweeps' launch shapes on this batch (real attempts on scratch
+    // state, re-initialised below), before the graph captures them
+    launch_prepare(w, s);
+    launch_to_f32(w->K.val64, w->K.val32, w->K.nnz_pad, s);
+    launch_to_f32(w->KT.val64, w->KT.val32, w->KT.nnz_pad, s);
+    int rc = autotune_batched<BP>(w, bt, a, B, l_b, u_b, s);
+    if (rc != PDHG_OK) return rc;
+  }
+  if (!o.host_loop) {
+    int rc = build_batched_graph<BP>(w, bt, a);
+    if (rc != PDHG_OK) return rc;
+  }
+  cudaEventRecord(w->ev[0], s);
+  launch_prepare(w, s);
+  launch_to_f32(w->K.val64, w->K.val32, w->K.nnz_pad, s);
+  launch_to_f32(w->KT.val64, w->KT.val32, w->KT.nnz_pad, s);
+  w->values_f32 = true;
+  batched_start<BP>(w, bt, a, B, l_b, u_b, s);
   if (o.host_loop) {
     // the graph body's kernels launched from the host (profilers cannot see
     // kernels inside a graph with conditional nodes); one wait per check
@@ -1309,7 +1437,8 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
       return PDHG_ERR_CUDA;
     }
   }
-  kb_output<BP><<<gv, 256, 0, s>>>(a, w->perm_col, w->perm_row, w->Dc, w->Dr, x_out, y_out);
+  kb_output<BP><<<std::min(w->num_sms * 8, 8192), 256, 0, s>>>(a, w->perm_col, w->perm_row, w->Dc, w->Dr,
+                                                               x_out, y_out);
   cudaEventRecord(w->ev[1], s);
   if (cudaMemcpyAsync(bt->inst_host, bt->inst, sizeof(BInst) * BP, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
@@ -1358,6 +1487,15 @@ int solve_batched_impl(Workspace* w, int B, const double* l_b, const double* u_b
 }
 
 }  // namespace
+
+void batched_tuning(Workspace* w, int32_t* out) {
+  const Batched* bt = (const Batched*)w->batched;
+  const bool t = bt && bt->tuned;
+  out[0] = t ? bt->rw_dual : -1;
+  out[1] = t ? bt->grid_rows : 0;
+  out[2] = t ? bt->rw_adj : -1;
+  out[3] = t ? bt->grid_cols : 0;
+}
 
 void release_batched(Workspace* w) {
   Batched* bt = (Batched*)w->batched;

@@ -271,10 +271,12 @@ class Workspace:
         return a[: min(na.value, cap_a)], c[: min(nc.value, cap_c)]
 
     def tuning(self):
-        cfg = (C.c_int32 * 8)()
+        cfg = (C.c_int32 * 12)()
         _check(lib().pdhg_get_tuning(self.ws, cfg), "pdhg_get_tuning")
         names = ("unroll_dual", "grid_dual", "unroll_adj", "grid_adj")
-        return {"fp64": dict(zip(names, cfg[0:4])), "fp32": dict(zip(names, cfg[4:8]))}
+        bnames = ("rows_per_warp_dual", "grid_dual", "rows_per_warp_adj", "grid_adj")
+        return {"fp64": dict(zip(names, cfg[0:4])), "fp32": dict(zip(names, cfg[4:8])),
+                "batched": dict(zip(bnames, cfg[8:12]))}
 
     def time_kernels(self, precision=PREC_FP64, reps=20, stream=None):
         md, ma, bd, ba = C.c_double(), C.c_double(), C.c_double(), C.c_double()

@@ -34,6 +34,9 @@ def test_batched_matches_single_solves(B, tol):
     ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=tol, time_limit_s=300.0))
     xb, yb, rb = ws.solve_batched(l_b, u_b)
     xb, yb = xb.cpu().numpy(), yb.cpu().numpy()
+    tb = ws.tuning()["batched"]  # the batched autotuner ran and chose a shape
+    assert tb["rows_per_warp_dual"] in (1, 2, 4) and tb["rows_per_warp_adj"] in (1, 2, 4)
+    assert tb["grid_dual"] > 0 and tb["grid_adj"] > 0
     alone = set(np.linspace(0, B - 1, min(B, 8)).round().astype(int).tolist())
     for k in range(B):
         assert rb[k]["status_name"] == "optimal", (k, rb[k])
