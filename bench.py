@@ -52,8 +52,14 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--attempts", type=int, default=4096, help="step attempts per solver call")
-    p.add_argument("--ttt-limit", type=float, default=40.0,
-                   help="seconds cap of each time-to-tolerance solve (0 = skip)")
+    p.add_argument("--ttt-limit", type=float, default=300.0,
+                   help="seconds cap of the mixed-precision time-to-tolerance solve (0 = skip)")
+    p.add_argument("--ttt-limit-fp64", type=float, default=360.0,
+                   help="seconds cap of the FP64 time-to-tolerance solve")
+    p.add_argument("--ttt-small", default="uc24_g33_T24",
+                   help="workload solved to rel-KKT 1e-8 in both precisions beside the capped large solves")
+    p.add_argument("--cpu-ttt-limit", type=float, default=60.0,
+                   help="seconds cap of each CPU oracle time-to-tolerance solve (0 = skip)")
     p.add_argument("--cpu-attempts", type=int, default=64, help="oracle attempts of the CPU sample")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-variant", type=int, default=-1,
@@ -183,6 +189,51 @@ def cpu_oracle_gbs(inst, attempts: int):
     d, a = algorithmic_bytes(inst.n, inst.m, inst.nnz, 8)
     gbs = attempts * (d + a) / dt / 1e9
     return gbs, dt
+
+
+def cpu_oracle_ttt(names, cap_s: float) -> dict:
+    """The CPU oracle's own time to rel-KKT 1e-4 / 1e-6 / 1e-8 (one core, capped):
+    seconds and attempts when each level was first reached at a check, -1 if not
+    within the cap."""
+    from oracle.lp import lp_from_arrays
+    from oracle.pdhg import pdhg_solve
+    from paper_2512_06715_gb300.instances import workload
+    out = {}
+    for name in names:
+        inst = workload(name)
+        lp = lp_from_arrays(inst.row_ptr, inst.col, inst.val, inst.q, inst.c, inst.l, inst.u, inst.m_eq)
+        t0 = time.perf_counter()
+        stamps = {}
+
+        def on_check(k, rel):
+            now = time.perf_counter() - t0
+            for t in (1e-4, 1e-6, 1e-8):
+                if rel <= t and t not in stamps:
+                    stamps[t] = (now, k)
+            return now >= cap_s
+
+        res = pdhg_solve(lp, tol=1e-8, max_attempts=10**9, on_check=on_check)
+        out[name] = {"cores": 1, "cap_s": cap_s, "status": res.status, "rel_kkt": res.rel_kkt,
+                     "attempts": res.attempts, "seconds": time.perf_counter() - t0,
+                     "seconds_to_1e-4_1e-6_1e-8": [stamps.get(t, (-1.0, -1))[0] for t in (1e-4, 1e-6, 1e-8)],
+                     "attempts_to_1e-4_1e-6_1e-8": [stamps.get(t, (-1.0, -1))[1] for t in (1e-4, 1e-6, 1e-8)]}
+    return out
+
+
+def cpu_recheck(returned: dict, insts: dict) -> dict:
+    """The oracle's rel-KKT and objective of each point the GPU returned in the
+    time-to-tolerance solves (the library's reported values beside them)."""
+    from oracle.lp import kkt, lp_from_arrays
+    from paper_2512_06715_gb300.instances import workload
+    out = {}
+    for key, (x, y, r) in returned.items():
+        name = key.split("@")[1] if "@" in key else next(iter(insts))
+        inst = insts.get(name) or workload(name)
+        lp = lp_from_arrays(inst.row_ptr, inst.col, inst.val, inst.q, inst.c, inst.l, inst.u, inst.m_eq)
+        k = kkt(lp, x, y)
+        out[key] = {"oracle_rel_kkt": k.rel_kkt, "oracle_primal_obj": k.primal_obj,
+                    "reported_rel_kkt": r["rel_kkt"], "reported_primal_obj": r["primal_obj"]}
+    return out
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -440,18 +491,42 @@ def run_ours(args):
     e2e = {"value": world * e_att * (d32 + a32) / e2e_s / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # time to tolerance (capped), both precisions
+    # time to tolerance: the large LP in both precisions (capped), the small one to 1e-8
     ttt = {}
+    returned = {}  # points the CPU leg re-checks with the oracle
     if args.ttt_limit > 0:
-        for prec in ("mixed", "fp64"):
+        for prec, cap in (("mixed", args.ttt_limit), ("fp64", args.ttt_limit_fp64)):
             ws.set_opts(precision=pdhg.PREC_MIXED if prec == "mixed" else pdhg.PREC_FP64,
-                        max_iters=10**9, tol=1e-8, time_limit_s=args.ttt_limit)
-            _, _, r = ws.solve()
+                        max_iters=10**9, tol=1e-8, time_limit_s=cap)
+            x, y, r = ws.solve()
+            returned[prec] = (x.cpu().numpy(), y.cpu().numpy(), r)
             ttt[prec] = {"status": r["status_name"], "rel_kkt": r["rel_kkt"],
                          "seconds_to_1e-4_1e-6_1e-8": r["time_to_tol"],
                          "attempts_to_1e-4_1e-6_1e-8": r["iters_to_tol"],
-                         "cap_s": args.ttt_limit, "attempts": r["iterations"],
-                         "attempts_per_s": r["iterations"] / r["solve_seconds"]}
+                         "cap_s": cap, "attempts": r["iterations"],
+                         "attempts_per_s": r["iterations"] / r["solve_seconds"], "omega": r["omega"],
+                         "ir_rounds": r["ir_rounds"], "primal_obj": r["primal_obj"]}
+        ratios = {}
+        for i, t in enumerate(("1e-4", "1e-6", "1e-8")):
+            a_m, a_f = ttt["mixed"]["seconds_to_1e-4_1e-6_1e-8"][i], ttt["fp64"]["seconds_to_1e-4_1e-6_1e-8"][i]
+            ratios[t] = (a_f / a_m) if (a_m > 0 and a_f > 0) else None
+        ttt["fp64_over_mixed_seconds"] = ratios
+        # the small relaxation, both precisions to 1e-8
+        inst_s = workload(args.ttt_small)
+        small = {}
+        for prec in ("mixed", "fp64"):
+            w2 = pdhg.Workspace.from_instance(inst_s, pdhg.default_opts(precision=prec, tol=1e-8, time_limit_s=300.0),
+                                              device=dev)
+            w2.solve()  # tuning, graph
+            x2, y2, r2 = w2.solve()
+            returned[f"{prec}@{args.ttt_small}"] = (x2.cpu().numpy(), y2.cpu().numpy(), r2)
+            w2.close()
+            small[prec] = {"status": r2["status_name"], "rel_kkt": r2["rel_kkt"], "seconds": r2["solve_seconds"],
+                           "attempts": r2["iterations"], "seconds_to_1e-4_1e-6_1e-8": r2["time_to_tol"]}
+        s_m, s_f = small["mixed"]["seconds"], small["fp64"]["seconds"]
+        small["fp64_over_mixed_seconds_to_1e-8"] = s_f / s_m if (small["mixed"]["status"] == "optimal" and
+                                                                 small["fp64"]["status"] == "optimal") else None
+        ttt[args.ttt_small] = small
 
     nodes = (node_throughput(args, dev, stream, pdhg, world, rank)
              if (args.nodes_attempts > 0 or args.nodes_tol > 0) else None)
@@ -461,6 +536,9 @@ def run_ours(args):
         gbs, dt = cpu_oracle_gbs(inst, args.cpu_attempts)
         cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_attempts} oracle attempts (rescaling included) on {args.workload}, {dt:.1f} s"}
+        if args.cpu_ttt_limit > 0:
+            cpu["time_to_tolerance"] = cpu_oracle_ttt([args.ttt_small, "uc4224_g600_T48"], args.cpu_ttt_limit)
+        cpu["gpu_points_rechecked"] = cpu_recheck(returned, {args.workload: inst})
 
     if rank == 0:
         line = {

@@ -146,7 +146,7 @@ def _kkt_omega(slp: LP, Dr, Dc, lp: LP, x_s, y_s, omega):
 
 def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: PDLPOptions | None = None,
                schedule: dict | None = None, fixed: dict | None = None, record: bool = False,
-               stop_after: int | None = None, start: tuple | None = None) -> PDHGResult:
+               stop_after: int | None = None, start: tuple | None = None, on_check=None) -> PDHGResult:
     """Solve ``lp`` to rel-KKT <= tol.
 
     fixed      -- dict(eta=..., omega=...): constant steps, every attempt accepted, no
@@ -154,6 +154,8 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
     schedule   -- dict(attempts=[(eta, accepted), ...], checks=[(restart, to_avg), ...])
     stop_after -- stop after this many attempts (status "stopped").
     start      -- (x, y) of the ORIGINAL LP to start from instead of the projection of 0.
+    on_check   -- called as on_check(attempts, best rel_kkt) at every check; returning
+                  True stops the solve (status "stopped"), e.g. at a wall-clock cap.
     """
     opts = opts or PDLPOptions()
     slp, Dr, Dc = rescale(lp, opts.ruiz_iters, opts.pock_chambolle)
@@ -236,6 +238,12 @@ def pdhg_solve(lp: LP, tol: float = 1e-8, max_attempts: int = 1_000_000, opts: P
         entry = dict(attempts=k, kkt_cur=kc_cur, kkt_avg=kc_avg, rel_cur=res_cur.rel_kkt,
                      rel_avg=res_avg.rel_kkt, omega=omega)
         best_avg = res_avg.rel_kkt < res_cur.rel_kkt
+        if on_check is not None and on_check(k, min(res_cur.rel_kkt, res_avg.rel_kkt)) and \
+                min(res_cur.rel_kkt, res_avg.rel_kkt) > tol:
+            final = (xbar, ybar, res_avg) if best_avg else (x, y, res_cur)
+            status = "stopped"
+            check_log.append(entry)
+            break
         if min(res_cur.rel_kkt, res_avg.rel_kkt) <= tol:
             final = (xbar, ybar, res_avg) if best_avg else (x, y, res_cur)
             status = "optimal"
