@@ -143,14 +143,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dual_kernel_name(variant: int, t: str = "float") -> str:
-    """Template name of the K x' kernel a tuning variant launches (0, 9: the
-    pipelined form; 8, 9: compiled for 8 resident blocks per SM)."""
-    if variant in (0, 9):
-        return f"k_dual_pipe<{t}, {8 if variant == 9 else 1}>"
-    if variant == 8:
-        return f"k_dual<{t}, 1, 8>"
-    return f"k_dual<{t}, {variant}, 1>"
+def dual_kernel_name(variant: int) -> str:
+    """Template name of the FP32 K x' kernel a tuning variant launches (the
+    second template argument of the sliced-ELL forms is the number of resident
+    blocks per SM they are compiled for)."""
+    return {0: "k_dual_pipe<float, 5>", 1: "k_dual<float, 1, 6>", 2: "k_dual<float, 2, 4>",
+            4: "k_dual<float, 4, 4>", 8: "k_dual<float, 1, 8>", 9: "k_dual_pipe<float, 8>",
+            16: "k_dual_staged<float, 1>", 17: "k_dual_staged<float, 2>"}.get(variant, f"variant {variant}")
 
 
 def measured_peaks() -> dict:

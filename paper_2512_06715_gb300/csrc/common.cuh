@@ -287,7 +287,9 @@ __device__ __forceinline__ double step_power(int64_t k1, double e) {
   return (double)exp2f(-(float)e * log2f((float)k1));
 }
 
-// FP32 iterations take tau = eta / omega and sigma = eta * omega in FP32.  When
+// FP32 iterations take tau = eta / omega and sigma = eta * omega in FP32.  The
+// cap is applied once per check (k_control), where the FP64 division costs
+// nothing per attempt; between checks eta grows by at most a factor ~1.3.  When
 // the step-size rule finds no interaction (eta_max = inf, e.g. a primal iterate
 // pinned at its bounds while the dual diverges on an infeasible LP) it grows eta
 // by (1 + (k+1)^-0.6) per attempt, which leaves the FP32 range within ~10^4
@@ -334,7 +336,6 @@ __device__ void decide_step(DevState* st, const IterArgs<T>& a, double dy2, doub
   const int64_t kg = st->k_offset + k;
   double eta_next = fmin((1.0 - step_power(kg + 1, st->red_exp)) * eta_max,
                          (1.0 + step_power(kg + 1, st->grow_exp)) * eta);
-  if (sizeof(T) == 4) eta_next = fmin(eta_next, fp32_step_cap(omega));
   int accept = eta <= eta_max;
   if (st->fixed) {
     accept = 1;

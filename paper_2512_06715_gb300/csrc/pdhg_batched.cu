@@ -311,10 +311,8 @@ __global__ void __launch_bounds__(kBThreads) kb_dual(BArgs<BP> a) {
         I.k += 1;
         I.k_total += 1;
         // attempts of all rounds (a refinement round is a change of coordinates)
-        const double eta_next =
-            fmin(fmin((1.0 - step_power(I.k_total + 1, g->red_exp)) * eta_max,
-                      (1.0 + step_power(I.k_total + 1, g->grow_exp)) * eta),
-                 fp32_step_cap(omega));
+        const double eta_next = fmin((1.0 - step_power(I.k_total + 1, g->red_exp)) * eta_max,
+                                     (1.0 + step_power(I.k_total + 1, g->grow_exp)) * eta);
         const int accept = eta <= eta_max;
         if (accept) {
           I.par = 1 - I.par;
@@ -787,6 +785,7 @@ __global__ void __launch_bounds__(256) kb_control(BArgs<BP> a, int nb_row, int n
         }
       }
     }
+    if (I.act) I.eta = fmin(I.eta, fp32_step_cap(I.omega));  // FP32 range (see fp32_step_cap)
     if (!I.done) atomicAdd(&s_running, 1);
   }
   __syncthreads();
@@ -1340,7 +1339,7 @@ int autotune_batched(Workspace* w, Batched* bt, const BArgs<BP>& a, int B, const
             kBThreads, 0);
       occ = std::max(occ, 1);
       const int need = (int)std::max<int64_t>(1, (len + 8 * kBWarps - 1) / (8 * kBWarps));
-      for (int bps = 1; bps <= std::min(occ, 4); ++bps) {
+      for (int bps = 1; bps <= std::min(occ, 8); ++bps) {
         const int g = std::min(std::min(sms * bps, need), 8192);
         auto run = [&]() {
           if (which == 0)

@@ -637,31 +637,44 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
 // the HBM and L2 latency at the cost of the spills; 16 and 17 stage the matrix
 // in shared memory with bulk copies (pdhg_staged.cu), one or two slices per
 // warp at a time.
+// Minimum resident blocks per SM that each variant is compiled for: the
+// register budget that keeps the one-slice forms at 6 (FP32) or 5 (FP64)
+// blocks per SM without spills (an unconstrained build takes ~58 registers and
+// drops to 4 blocks per SM).
+template <class T, int U>
+struct MinBlocks {
+  static constexpr int value = U == 1 ? (sizeof(T) == 4 ? 6 : 5) : (sizeof(T) == 4 ? 4 : 3);
+};
+template <class T>
+struct MinBlocksPipe {
+  static constexpr int value = sizeof(T) == 4 ? 5 : 3;
+};
+
 template <class T>
 void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
-    case 0: k_dual_pipe<T, 1><<<grid, kBlock, 0, s>>>(a); break;
-    case 2: k_dual<T, 2, 1><<<grid, kBlock, 0, s>>>(a); break;
-    case 4: k_dual<T, 4, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 0: k_dual_pipe<T, MinBlocksPipe<T>::value><<<grid, kBlock, 0, s>>>(a); break;
+    case 2: k_dual<T, 2, MinBlocks<T, 2>::value><<<grid, kBlock, 0, s>>>(a); break;
+    case 4: k_dual<T, 4, MinBlocks<T, 4>::value><<<grid, kBlock, 0, s>>>(a); break;
     case 8: k_dual<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 9: k_dual_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 16: launch_dual_staged<T>(a, grid, s, 1); break;
     case 17: launch_dual_staged<T>(a, grid, s, 2); break;
-    default: k_dual<T, 1, 1><<<grid, kBlock, 0, s>>>(a); break;
+    default: k_dual<T, 1, MinBlocks<T, 1>::value><<<grid, kBlock, 0, s>>>(a); break;
   }
 }
 
 template <class T>
 void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
-    case 0: k_adjoint_pipe<T, 1><<<grid, kBlock, 0, s>>>(a); break;
-    case 2: k_adjoint<T, 2, 1><<<grid, kBlock, 0, s>>>(a); break;
-    case 4: k_adjoint<T, 4, 1><<<grid, kBlock, 0, s>>>(a); break;
+    case 0: k_adjoint_pipe<T, MinBlocksPipe<T>::value><<<grid, kBlock, 0, s>>>(a); break;
+    case 2: k_adjoint<T, 2, MinBlocks<T, 2>::value><<<grid, kBlock, 0, s>>>(a); break;
+    case 4: k_adjoint<T, 4, MinBlocks<T, 4>::value><<<grid, kBlock, 0, s>>>(a); break;
     case 8: k_adjoint<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 9: k_adjoint_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 16: launch_adjoint_staged<T>(a, grid, s, 1); break;
     case 17: launch_adjoint_staged<T>(a, grid, s, 2); break;
-    default: k_adjoint<T, 1, 1><<<grid, kBlock, 0, s>>>(a); break;
+    default: k_adjoint<T, 1, MinBlocks<T, 1>::value><<<grid, kBlock, 0, s>>>(a); break;
   }
 }
 
@@ -671,8 +684,10 @@ void launch_state_init(DevState* st, const RoundInit& r, const double* scalars, 
 
 int blocks_per_sm_iter() {
   int best = 1 << 30;
-  const void* fns[4] = {(const void*)&k_dual<double, 1, 1>, (const void*)&k_adjoint<double, 1, 1>,
-                        (const void*)&k_dual<float, 1, 1>, (const void*)&k_adjoint<float, 1, 1>};
+  const void* fns[4] = {(const void*)&k_dual<double, 1, MinBlocks<double, 1>::value>,
+                        (const void*)&k_adjoint<double, 1, MinBlocks<double, 1>::value>,
+                        (const void*)&k_dual<float, 1, MinBlocks<float, 1>::value>,
+                        (const void*)&k_adjoint<float, 1, MinBlocks<float, 1>::value>};
   for (const void* f : fns) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0) != cudaSuccess) b = 4;

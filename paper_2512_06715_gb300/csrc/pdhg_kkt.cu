@@ -371,6 +371,7 @@ __global__ void __launch_bounds__(kBlock) k_control(IterArgs<T> a, int nb_row, i
     st->pobj = P[0];
     st->dobj = D[0];
   }
+  if (sizeof(T) == 4) st->eta = fmin(st->eta, fp32_step_cap(st->omega));
   st->restart_now = restart;
   st->restart_to_avg = to_avg;
   st->done = done;
