@@ -73,8 +73,11 @@ def parse():
     p.add_argument("--nodes-tol", type=float, default=0.0,
                    help="> 0: solve every node to this rel-KKT instead (converged node LPs/s)")
     p.add_argument("--nodes-cap", type=float, default=600.0, help="seconds cap of the converged node solves")
-    p.add_argument("--nodes-seq", type=int, default=1,
+    p.add_argument("--nodes-seq", type=int, default=2,
                    help="nodes solved one at a time for the sequential comparison")
+    p.add_argument("--nodes-conv-workload", default="uc200_g60_T24_slack",
+                   help="node LPs solved to --nodes-conv-tol (converged node LPs/s)")
+    p.add_argument("--nodes-conv-tol", type=float, default=1e-6, help="0: skip the converged node measurement")
     p.add_argument("--host-loop", action="store_true",
                    help="launch the per-check bodies from the host instead of one CUDA graph "
                         "(same kernels; profilers cannot see kernels inside conditional graphs)")
@@ -296,7 +299,7 @@ def gather_node_results(local: list, start: int, world: int) -> list:
     return out
 
 
-def node_throughput(args, dev, stream, pdhg, world=1, rank=0):
+def node_throughput(args, dev, stream, pdhg, world=1, rank=0, workload_name=None, tol=None):
     """Node LPs of one shared K (64 seeded commitment fixings), partitioned
     over the ranks (node_partition) and solved by each rank in one
     pdhg_solve_batched call, against the same nodes solved one at a time.
@@ -306,14 +309,16 @@ def node_throughput(args, dev, stream, pdhg, world=1, rank=0):
     import torch
     from paper_2512_06715_gb300.instances import node_fixings, workload
 
-    inst = workload(args.nodes_workload)
+    workload_name = workload_name or args.nodes_workload
+    tol = args.nodes_tol if tol is None else tol
+    inst = workload(workload_name)
     B = args.nodes
     l_np, u_np = node_fixings(inst, B)
     start, stop = node_partition(B, world, rank)
-    converged = args.nodes_tol > 0
+    converged = tol > 0
     kw = dict(precision="mixed", host_loop=int(args.host_loop), autotune=int(not args.no_autotune))
     if converged:
-        o = pdhg.default_opts(tol=args.nodes_tol, max_iters=10**9, time_limit_s=args.nodes_cap, **kw)
+        o = pdhg.default_opts(tol=tol, max_iters=10**9, time_limit_s=args.nodes_cap, **kw)
     else:
         o = pdhg.default_opts(tol=1e-12, max_iters=args.nodes_attempts, time_limit_s=600.0, **kw)
 
@@ -356,14 +361,14 @@ def node_throughput(args, dev, stream, pdhg, world=1, rank=0):
             t_seq.append(t1)
             att_seq.append(r1["iterations"])
     total_att = sum(n["attempts"] for n in nodes)
-    out = {"workload": args.nodes_workload, "n": inst.n, "m": inst.m, "nnz": inst.nnz, "nodes": B,
+    out = {"workload": workload_name, "n": inst.n, "m": inst.m, "nnz": inst.nnz, "nodes": B,
            "ranks": world, "partition": [list(node_partition(B, world, r)) for r in range(world)],
            "batched_tuning": tuning}
     if converged:
         att = np.array([n["attempts"] for n in nodes])
         statuses = sorted({n["status"] for n in nodes})
         t_seq_total = float(np.mean(t_seq)) * B if t_seq else None
-        out.update({"tol": args.nodes_tol, "cap_s": args.nodes_cap, "statuses": statuses,
+        out.update({"tol": tol, "cap_s": args.nodes_cap, "statuses": statuses,
                     "optimal": sum(n["status"] == "optimal" for n in nodes),
                     "batched_s": tb, "batched_node_lps_per_s": B / tb,
                     "sequential_node_lps_per_s": (B / t_seq_total) if t_seq_total else None,
@@ -529,6 +534,8 @@ def run_ours(args):
 
     nodes = (node_throughput(args, dev, stream, pdhg, world, rank)
              if (args.nodes_attempts > 0 or args.nodes_tol > 0) else None)
+    nodes_conv = (node_throughput(args, dev, stream, pdhg, world, rank, args.nodes_conv_workload,
+                                  args.nodes_conv_tol) if args.nodes_conv_tol > 0 else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -552,6 +559,7 @@ def run_ours(args):
             "fp64_gbs": fp64_gbs,
             "time_to_tolerance": ttt,
             "node_lps": nodes,
+            "node_lps_converged": nodes_conv,
             "roofline": roofline,
             "gpu_launches": launches,
             "kernel_tuning": ws.tuning(),

@@ -195,6 +195,8 @@ WORKLOADS = {
     "uc6049_g850_T48_slack": dict(n_bus=6049, n_line=8470, n_gen=850, n_periods=48, with_slack=True),
     # 4224-bus network, 600 generators, 24 hourly periods
     "uc4224_g600_T24": dict(n_bus=4224, n_line=5900, n_gen=600, n_periods=24),
+    # 200-bus network, 60 generators, 24 hourly periods, with shed/spill slacks
+    "uc200_g60_T24_slack": dict(n_bus=200, n_line=300, n_gen=60, n_periods=24, with_slack=True),
 }
 
 # The horizons of the GO Challenge 3 divisions the paper solves (Sec. II.B,
