@@ -58,6 +58,11 @@ def parse():
                    help="seconds cap of the FP64 time-to-tolerance solve")
     p.add_argument("--ttt-small", default="uc24_g33_T24",
                    help="workload solved to rel-KKT 1e-8 in both precisions beside the capped large solves")
+    p.add_argument("--ttt-trace", default="",
+                   help="directory: record the per-check trace of the capped time-to-tolerance solves "
+                        "there (numpy arrays and a markdown summary)")
+    p.add_argument("--ttt-opt", action="append", default=[],
+                   help="extra solver option name=value for the time-to-tolerance solves (repeatable)")
     p.add_argument("--cpu-ttt-limit", type=float, default=60.0,
                    help="seconds cap of each CPU oracle time-to-tolerance solve (0 = skip)")
     p.add_argument("--cpu-attempts", type=int, default=64, help="oracle attempts of the CPU sample")
@@ -191,6 +196,29 @@ def cpu_oracle_gbs(inst, attempts: int):
     d, a = algorithmic_bytes(inst.n, inst.m, inst.nnz, 8)
     gbs = attempts * (d + a) / dt / 1e9
     return gbs, dt
+
+
+def write_trace(out_dir: Path, tag: str, checks, r: dict, extra: dict):
+    """Per-check trace of a solve: the array (columns as pdhg_get_trace documents)
+    and a markdown table of about 40 evenly spaced checks plus every restart."""
+    out_dir.mkdir(parents=True, exist_ok=True)
+    np.save(out_dir / f"trace_{tag}.npy", checks)
+    lines = [f"# Per-check trace: {tag}", "",
+             f"Options beyond the defaults: {extra or 'none'}.  Final status {r['status_name']}, "
+             f"rel-KKT {r['rel_kkt']:.3e}, {r['iterations']} attempts, {r['restarts']} restarts, "
+             f"{r['ir_rounds']} refinement rounds, primal weight {r['omega']:.4g}; seconds to 1e-4/1e-6/1e-8: "
+             f"{[round(t, 2) for t in r['time_to_tol']]}.", "",
+             "| attempts | restart (to avg) | omega after | rel-KKT current / average | rel_p | rel_d | rel_gap |",
+             "|---|---|---|---|---|---|---|"]
+    if len(checks):
+        idx = sorted(set(np.linspace(0, len(checks) - 1, 40).round().astype(int).tolist()) |
+                     set(np.where(checks[:, 1] > 0)[0].tolist()))
+        for i in idx:
+            c = checks[i]
+            rs = ("yes (avg)" if c[2] else "yes") if c[1] else ""
+            lines.append(f"| {int(c[0])} | {rs} | {c[3]:.4g} | {c[6]:.2e} / {c[7]:.2e} | {c[8]:.2e} | "
+                         f"{c[9]:.2e} | {c[10]:.2e} |")
+    (out_dir / f"trace_{tag}.md").write_text("\n".join(lines) + "\n")
 
 
 def cpu_oracle_ttt(names, cap_s: float) -> dict:
@@ -499,10 +527,16 @@ def run_ours(args):
     ttt = {}
     returned = {}  # points the CPU leg re-checks with the oracle
     if args.ttt_limit > 0:
+        extra = {}
+        for kv in args.ttt_opt:
+            k, v = kv.split("=")
+            extra[k] = float(v) if any(ch in v for ch in ".e") else int(v)
         for prec, cap in (("mixed", args.ttt_limit), ("fp64", args.ttt_limit_fp64)):
             ws.set_opts(precision=pdhg.PREC_MIXED if prec == "mixed" else pdhg.PREC_FP64,
-                        max_iters=10**9, tol=1e-8, time_limit_s=cap)
+                        max_iters=10**9, tol=1e-8, time_limit_s=cap, trace=int(bool(args.ttt_trace)), **extra)
             x, y, r = ws.solve()
+            if args.ttt_trace:
+                write_trace(Path(args.ttt_trace), f"{args.workload}_{prec}", ws.trace()[1], r, extra)
             returned[prec] = (x.cpu().numpy(), y.cpu().numpy(), r)
             ttt[prec] = {"status": r["status_name"], "rel_kkt": r["rel_kkt"],
                          "seconds_to_1e-4_1e-6_1e-8": r["time_to_tol"],
