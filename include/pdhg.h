@@ -115,10 +115,10 @@ typedef struct pdhg_opts {
                                fastest; 0: fixed defaults (1)                         */
   volatile int32_t *cancel_flag; /* host-mapped int polled at every check, or NULL    */
   int32_t kernel_variant;   /* -1: the autotuner decides, variant 1 when autotune is 0;
-                               0, 1, 2, 4, 8, 9: that variant of both per-attempt
-                               kernels, as reported by pdhg_get_tuning, with the
-                               default grid; read at the first solve of each
-                               precision; default -1                                */
+                               0, 1, 2, 4, 8, 9, 16-19: that variant of both
+                               per-attempt kernels, as reported by pdhg_get_tuning,
+                               with the default grid; read at the first solve of
+                               each precision; default -1                          */
   int32_t kernel_grid;      /* > 0: blocks of both per-attempt kernels, overriding the
                                autotuner's grid; small grids make each warp sweep
                                many slices; 0: default or autotuned; default 0       */
@@ -308,8 +308,10 @@ int pdhg_get_trace(void *ws, double *attempts, int64_t cap_a, double *checks, in
  * unroll 1, 2, 4: 32-row slices a warp sweeps together; 0: one slice per warp,
  * software pipelined (the next slice's first entries and row operands are
  * loaded while the current slice's gathers are in flight); 8, 9: variants 1
- * and 0 compiled for 8 resident blocks per SM (32 registers).  A precision not
- * yet solved reports unroll -1 and grid 0. */
+ * and 0 compiled for 8 resident blocks per SM (32 registers); 16, 17: the matrix
+ * staged in shared memory by TMA bulk copies, one or two slices per warp at a
+ * time; 18, 19: the same with the row (column) operands staged too.  A
+ * precision not yet solved reports unroll -1 and grid 0. */
 int pdhg_get_tuning(void *ws, int32_t *cfg);
 
 /* Launch the two per-attempt kernels of `precision` `reps` times each on

@@ -33,6 +33,7 @@ CUDA_SOURCES = [
     "pdhg_adjoint.cu",
     "pdhg_noalloc.cu",
     "pdhg_staged.cu",
+    "pdhg_rowstaged.cu",
 ]
 
 

@@ -18,13 +18,15 @@ constexpr int kMaxBlocks = 8192; // upper bound of the persistent grid sizes
 constexpr int kRowSums = 7;      // per-candidate sums of the row-side KKT kernel
 constexpr int kColSums = 9;      // per-candidate sums of the column-side KKT kernel
 constexpr int kRegionStride = 24;  // doubles per block in each partials region (>= 2 x sums)
-constexpr int kStageEntries = 3072;
+constexpr int kStageEntries = 3072;  // sliced-ELL entries per shared-memory chunk (staged kernels)
+constexpr int kRsEntries = 2048;     // entries per chunk of the row-staged kernels
+constexpr int kRsSlices = 32;        // slices per chunk of the row-staged kernels
 // Certificate tolerance floor for rays made of FP32 iterates: differences of
 // FP32 vectors carry ~1e-7 relative noise, so their violation/objective ratio
 // cannot fall below ~1e-7 however well the iteration has converged onto the
 // infeasibility direction; FP32 iterations therefore test rays at
 // max(infeas_tol, kFp32RayTol).
-constexpr double kFp32RayTol = 1e-6;  // sliced-ELL entries per shared-memory chunk (staged kernels)
+constexpr double kFp32RayTol = 1e-6;
 constexpr int kTraceCheckCols = 12;  // values recorded per KKT check in the trace
 
 // Sliced ELL with 32-row slices over the internal (length-sorted) row order.
@@ -131,6 +133,10 @@ struct IterArgs {
   const int32_t* kchunks;
   const int32_t* tchunks;
   int32_t kchunks_n, tchunks_n;
+  // chunks of the row-staged kernels (<= kRsEntries entries, <= kRsSlices slices)
+  const int32_t* kchunks2;
+  const int32_t* tchunks2;
+  int32_t kchunks2_n, tchunks2_n;
   unsigned long long cond;  // cudaGraphConditionalHandle
   int32_t in_graph;
   // FP64 data of the KKT evaluation

@@ -20,6 +20,8 @@ struct DevSell {
   float* val32 = nullptr;
   int32_t* chunks = nullptr;  // [nchunks + 1] slice boundaries of the staged chunks
   int32_t nchunks = 0;        // 0: a slice exceeds kStageEntries (no staged kernels)
+  int32_t* chunks2 = nullptr;  // chunks of the row-staged kernels
+  int32_t nchunks2 = 0;
   SellView<double> v64() const { return {off, col, val64, nslices, rows}; }
   SellView<float> v32() const { return {off, col, val32, nslices, rows}; }
 };
@@ -158,9 +160,16 @@ void launch_dual_staged(const IterArgs<T>& a, int grid, cudaStream_t s, int pair
 template <class T>
 void launch_adjoint_staged(const IterArgs<T>& a, int grid, cudaStream_t s, int pair);
 int staged_setup();
-// chunks of consecutive slices with at most kStageEntries entries each; false if
-// a single slice is larger
-bool build_chunks(const std::vector<int32_t>& off, std::vector<int32_t>* chunks);
+// pdhg_rowstaged.cu: the same with the row (column) operands staged too
+template <class T>
+void launch_dual_rowstaged(const IterArgs<T>& a, int grid, cudaStream_t s, int pair);
+template <class T>
+void launch_adjoint_rowstaged(const IterArgs<T>& a, int grid, cudaStream_t s, int pair);
+int rowstaged_setup();
+// chunks of consecutive slices with at most max_entries entries and max_slices
+// slices each; false if a single slice is larger
+bool build_chunks(const std::vector<int32_t>& off, std::vector<int32_t>* chunks, int max_entries,
+                  int max_slices);
 
 // pdhg_kkt.cu
 template <class T>

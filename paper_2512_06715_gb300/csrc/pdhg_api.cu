@@ -32,6 +32,9 @@ static int fail(int code, const std::string& msg) {
 template <class P>
 static cudaError_t dalloc(Workspace* w, P** p, size_t count) {
   void* q = nullptr;
+  // lengths rounded up to whole 32-row slices: the row-staged kernels copy the
+  // operand rows of whole slices
+  count = (count + 31) / 32 * 32;
   cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
   if (e == cudaSuccess) {
     w->allocs.push_back(q);
@@ -94,6 +97,10 @@ IterArgs<T> make_args(Workspace* w) {
   a.kchunks_n = w->K.nchunks;
   a.tchunks = w->KT.chunks;
   a.tchunks_n = w->KT.nchunks;
+  a.kchunks2 = w->K.chunks2;
+  a.kchunks2_n = w->K.nchunks2;
+  a.tchunks2 = w->KT.chunks2;
+  a.tchunks2_n = w->KT.nchunks2;
   a.cond = 0;
   a.in_graph = 0;
   a.K64 = w->K.v64();
@@ -183,10 +190,14 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   t.grid_dual = w->grid_k;
   t.grid_adj = w->grid_kt;
   if (!w->opts.autotune || fixed_variant >= 0) {
-    if (fixed_variant >= 16 &&
+    if ((fixed_variant == 16 || fixed_variant == 17) &&
         (w->K.nchunks == 0 || w->KT.nchunks == 0 || staged_setup() != 0))
       return fail(PDHG_ERR_UNSUPPORTED,
                   "kernel_variant 16/17: a slice exceeds the staged chunk size on this matrix");
+    if ((fixed_variant == 18 || fixed_variant == 19) &&
+        (w->K.nchunks2 == 0 || w->KT.nchunks2 == 0 || rowstaged_setup() != 0))
+      return fail(PDHG_ERR_UNSUPPORTED,
+                  "kernel_variant 18/19: a slice exceeds the row-staged chunk size on this matrix");
     if (w->opts.kernel_grid > 0) t.grid_dual = t.grid_adj = w->opts.kernel_grid;
     t.done = true;
     return PDHG_OK;
@@ -196,7 +207,8 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   // 8, 9: the one-slice and pipelined forms limited to 32 registers (8 blocks
   // per SM)
   const bool staged = w->K.nchunks > 0 && w->KT.nchunks > 0 && staged_setup() == 0;
-  const int unrolls[8] = {1, 2, 4, 0, 8, 9, 16, 17};
+  const bool rowstaged = w->K.nchunks2 > 0 && w->KT.nchunks2 > 0 && rowstaged_setup() == 0;
+  const int unrolls[10] = {1, 2, 4, 0, 8, 9, 16, 17, 18, 19};
   const int bps[5] = {2, 3, 4, 6, 8};
   // UCPDHG_TUNE_LOG=1 prints every timed candidate to stderr
   const char* log_env = std::getenv("UCPDHG_TUNE_LOG");
@@ -205,9 +217,10 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
     const int nsl = which == 0 ? w->K.nslices : w->KT.nslices;
     float best = 1e30f;
     int bu = 1, bg = which == 0 ? w->grid_k : w->grid_kt;
-    for (int ui = 0; ui < 8; ++ui) {
+    for (int ui = 0; ui < 10; ++ui) {
       const int U = unrolls[ui];
-      if (U >= 16 && !staged) continue;
+      if ((U == 16 || U == 17) && !staged) continue;
+      if ((U == 18 || U == 19) && !rowstaged) continue;
       const int Us = (U == 2 || U == 4) ? U : 1;
       const int need = (nsl + kWarps * Us - 1) / (kWarps * Us);
       for (int bi = 0; bi < 5; ++bi) {
@@ -315,8 +328,9 @@ static int validate_opts(const pdhg_opts* o) {
     return fail(PDHG_ERR_INVALID_ARG, "opts: fixed_eta needs fixed_omega > 0");
   if (!(o->kernel_variant == -1 || o->kernel_variant == 0 || o->kernel_variant == 1 ||
         o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 8 ||
-        o->kernel_variant == 9 || o->kernel_variant == 16 || o->kernel_variant == 17))
-    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8, 9, 16 or 17");
+        o->kernel_variant == 9 || o->kernel_variant == 16 || o->kernel_variant == 17 ||
+        o->kernel_variant == 18 || o->kernel_variant == 19))
+    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8, 9, 16, 17, 18 or 19");
   if (o->ir_fold_checks < 0)
     return fail(PDHG_ERR_INVALID_ARG, "opts: ir_fold_checks must be >= 0");
   if (!(o->infeas_tol >= 0.0))
@@ -642,10 +656,16 @@ extern "C" int pdhg_workspace_create(const pdhg_problem* prob, const pdhg_opts* 
   w->KT.rows = (int32_t)w->n;
   w->KT.nnz_pad = L.t_col.size();
   std::vector<int32_t> kch, tch;
-  if (build_chunks(L.k_off, &kch) && build_chunks(L.t_off, &tch)) {
+  if (build_chunks(L.k_off, &kch, kStageEntries, 1 << 30) && build_chunks(L.t_off, &tch, kStageEntries, 1 << 30)) {
     w->K.nchunks = (int32_t)kch.size() - 1;
     w->KT.nchunks = (int32_t)tch.size() - 1;
     if (up(&w->K.chunks, kch) || up(&w->KT.chunks, tch))
+      return bail(fail(PDHG_ERR_NOMEM, "device allocation/upload of the chunk tables failed"));
+  }
+  if (build_chunks(L.k_off, &kch, kRsEntries, kRsSlices) && build_chunks(L.t_off, &tch, kRsEntries, kRsSlices)) {
+    w->K.nchunks2 = (int32_t)kch.size() - 1;
+    w->KT.nchunks2 = (int32_t)tch.size() - 1;
+    if (up(&w->K.chunks2, kch) || up(&w->KT.chunks2, tch))
       return bail(fail(PDHG_ERR_NOMEM, "device allocation/upload of the chunk tables failed"));
   }
   if (up(&w->perm_row, L.perm_row) || up(&w->perm_col, L.perm_col) || up(&w->K.off, L.k_off) ||

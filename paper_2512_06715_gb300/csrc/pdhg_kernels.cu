@@ -636,7 +636,8 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
 // (at most 32 registers, a few spilled to L1) -- more warps in flight against
 // the HBM and L2 latency at the cost of the spills; 16 and 17 stage the matrix
 // in shared memory with bulk copies (pdhg_staged.cu), one or two slices per
-// warp at a time.
+// warp at a time; 18 and 19 stage the row (column) operands with the matrix
+// chunk (pdhg_rowstaged.cu).
 // Minimum resident blocks per SM that each variant is compiled for: the
 // register budget that keeps the one-slice forms at 6 (FP32) or 5 (FP64)
 // blocks per SM without spills (an unconstrained build takes ~58 registers and
@@ -660,6 +661,8 @@ void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
     case 9: k_dual_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 16: launch_dual_staged<T>(a, grid, s, 1); break;
     case 17: launch_dual_staged<T>(a, grid, s, 2); break;
+    case 18: launch_dual_rowstaged<T>(a, grid, s, 1); break;
+    case 19: launch_dual_rowstaged<T>(a, grid, s, 2); break;
     default: k_dual<T, 1, MinBlocks<T, 1>::value><<<grid, kBlock, 0, s>>>(a); break;
   }
 }
@@ -674,6 +677,8 @@ void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) 
     case 9: k_adjoint_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
     case 16: launch_adjoint_staged<T>(a, grid, s, 1); break;
     case 17: launch_adjoint_staged<T>(a, grid, s, 2); break;
+    case 18: launch_adjoint_rowstaged<T>(a, grid, s, 1); break;
+    case 19: launch_adjoint_rowstaged<T>(a, grid, s, 2); break;
     default: k_adjoint<T, 1, MinBlocks<T, 1>::value><<<grid, kBlock, 0, s>>>(a); break;
   }
 }

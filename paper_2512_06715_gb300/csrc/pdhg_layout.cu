@@ -122,17 +122,18 @@ int build_layout(int64_t n, int64_t m, int64_t m_eq, const std::vector<int64_t>&
   return PDHG_OK;
 }
 
-bool build_chunks(const std::vector<int32_t>& off, std::vector<int32_t>* chunks) {
+bool build_chunks(const std::vector<int32_t>& off, std::vector<int32_t>* chunks, int max_entries,
+                  int max_slices) {
   chunks->clear();
   const int32_t ns = (int32_t)off.size() - 1;
   chunks->push_back(0);
   int32_t s0 = 0;
   for (int32_t s = 0; s < ns; ++s) {
-    if (off[s + 1] - off[s] > kStageEntries) {
+    if (off[s + 1] - off[s] > max_entries) {
       chunks->clear();
       return false;
     }
-    if (off[s + 1] - off[s0] > kStageEntries) {
+    if (off[s + 1] - off[s0] > max_entries || s + 1 - s0 > max_slices) {
       chunks->push_back(s);
       s0 = s;
     }

@@ -22,49 +22,12 @@
 // DevState::wait_timeout, skips the remaining work of the chunk (keeping the
 // block's barriers), still drains the copies it issued (bounded again) and
 // the host reports PDHG_ERR_TIMEOUT.
-#include "internal.cuh"
+#include "staging.cuh"
 
 namespace ucpdhg {
 namespace {
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false if it never completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (int it = 0; it < (1 << 20); ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// 1-D bulk copy global -> shared, completing `bytes` on the barrier.  Both
-// addresses 16-byte aligned, bytes a multiple of 16 (chunk boundaries are
-// slice boundaries: multiples of 32 entries).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
+using namespace staging;
 
 // Shared-memory layout of a staged kernel: two barriers, then the two chunk
 // buffers of columns and of values.
@@ -99,87 +62,6 @@ __device__ __forceinline__ void issue_chunk(const SellView<T>& A, const int32_t*
   bulk_g2s(sm.val(b), A.val + e0, ne * (uint32_t)sizeof(T), &sm.bar[b]);
 }
 
-// Row products of P slices of the staged chunk at once (lane = row of each),
-// entries in predicated groups of 4 per slice, so the gathers of all P slices
-// of a group issue together before the first is consumed.
-template <class T, int P, bool TWO>
-__device__ __forceinline__ void staged_rows(const int32_t* __restrict__ scol, const T* __restrict__ sval,
-                                            const int (&o)[P], const int (&w)[P], const T* __restrict__ x1,
-                                            const T* __restrict__ x2, T (&acc1)[P], T (&acc2)[P]) {
-  int wmax = 0;
-#pragma unroll
-  for (int u = 0; u < P; ++u) {
-    acc1[u] = 0;
-    acc2[u] = 0;
-    wmax = max(wmax, w[u]);
-  }
-  for (int k0 = 0; k0 < wmax; k0 += 4) {
-    int c[P][4];
-    T v[P][4];
-#pragma unroll
-    for (int u = 0; u < P; ++u)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const bool ok = k0 + e < w[u];
-        c[u][e] = ok ? scol[o[u] + (k0 + e) * kSlice] : 0;
-        v[u][e] = ok ? sval[o[u] + (k0 + e) * kSlice] : (T)0;
-      }
-#pragma unroll
-    for (int u = 0; u < P; ++u)
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (k0 + e < w[u]) {
-          acc1[u] += v[u][e] * __ldg(x1 + c[u][e]);
-          if (TWO) acc2[u] += v[u][e] * __ldg(x2 + c[u][e]);
-        }
-  }
-}
-
-// Chunk pipeline shared by both kernels: thread 0 keeps two copies in flight;
-// `work(buffer, chunk)` runs when a chunk has landed.  Bounded waits: a
-// timeout marks the block aborted (it keeps its barriers, starts no copies,
-// skips the work) and thread 0 drains the copies it issued (bounded again).
-template <class T, class Work>
-__device__ __forceinline__ void run_chunks(const SellView<T>& A, const int32_t* chunks, int nch,
-                                           bool stream_matrix, Stage<T>& sm, int* s_abort, DevState* st,
-                                           Work&& work) {
-  const int G = gridDim.x;
-  const int nmine = (int)blockIdx.x < nch ? (nch - 1 - (int)blockIdx.x) / G + 1 : 0;
-  int issued = 0;  // thread 0: chunks whose copy was started
-  if (threadIdx.x == 0) {
-    *s_abort = 0;
-    if (stream_matrix) {
-      mbar_init(&sm.bar[0], 1);
-      mbar_init(&sm.bar[1], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && stream_matrix)
-    for (; issued < 2 && issued < nmine; ++issued) issue_chunk<T>(A, chunks, blockIdx.x + issued * G, sm, issued);
-  int first_pending = nmine;
-  for (int i = 0; i < nmine; ++i) {
-    const int b = i & 1;
-    bool ok = *s_abort == 0;
-    if (ok && stream_matrix) ok = mbar_wait(&sm.bar[b], (uint32_t)((i >> 1) & 1));
-    if (!ok) {
-      *s_abort = 1;
-      if (first_pending > i) first_pending = i;
-    }
-    if (ok) work(b, blockIdx.x + i * G);
-    __syncthreads();  // every warp is done with buffer b
-    if (threadIdx.x == 0 && stream_matrix && *s_abort == 0 && issued < nmine) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_chunk<T>(A, chunks, blockIdx.x + issued * G, sm, b);
-      ++issued;
-    }
-  }
-  if (threadIdx.x == 0 && *s_abort) {
-    st->wait_timeout = 1;
-    for (int k = first_pending; k < issued; ++k) mbar_wait(&sm.bar[k & 1], (uint32_t)((k >> 1) & 1));
-  }
-}
-
 }  // namespace
 
 template <class T, int P>
@@ -201,7 +83,8 @@ __global__ void __launch_bounds__(kBlock) k_dual_staged(IterArgs<T> a) {
   constexpr bool kStored = StoresKx<T>::value;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T acc_dy2 = 0, acc_int = 0;
-  run_chunks<T>(a.K, a.kchunks, a.kchunks_n, true, sm, &s_abort, st, [&](int b, int c) {
+  run_chunks(sm.bar, a.kchunks_n, true, &s_abort, st,
+             [&](int b, int c) { issue_chunk<T>(a.K, a.kchunks, c, sm, b); }, [&](int b, int c) {
     const int s0 = __ldg(a.kchunks + c), s1 = __ldg(a.kchunks + c + 1);
     const int base = __ldg(a.K.off + s0);
     for (int sg = s0 + warp; sg < s1; sg += kWarps * P) {
@@ -276,7 +159,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_staged(IterArgs<T> a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T acc_dx2 = 0;
   // a rejected step reuses the cached K^T y: no matrix stream at all
-  run_chunks<T>(a.KT, a.tchunks, a.tchunks_n, acc_last != 0, sm, &s_abort, st, [&](int b, int c) {
+  run_chunks(sm.bar, a.tchunks_n, acc_last != 0, &s_abort, st,
+             [&](int b, int c) { issue_chunk<T>(a.KT, a.tchunks, c, sm, b); }, [&](int b, int c) {
     const int s0 = __ldg(a.tchunks + c), s1 = __ldg(a.tchunks + c + 1);
     const int base = __ldg(a.KT.off + s0);
     for (int sg = s0 + warp; sg < s1; sg += kWarps * P) {

@@ -88,7 +88,7 @@ def test_spmv_and_scaling_parity(shape):
 
 
 @pytest.mark.parametrize("variant,grid", [(-1, 0), (1, 3), (2, 3), (4, 2), (0, 0), (0, 3), (8, 3), (9, 2),
-                                          (16, 0), (16, 3), (17, 2)])
+                                          (16, 0), (16, 3), (17, 2), (18, 0), (18, 3), (19, 2)])
 def test_fixed_step_iterates_match_oracle(tiny24, variant, grid):
     """Constant steps, no restarts: iterates after 128 attempts agree with the
     oracle to 1e-10 relative, for every variant of the per-attempt kernels
@@ -133,7 +133,7 @@ def test_solve_tiny_matches_oracle(tiny24, tiny24_oracle, precision):
     assert r["time_to_tol"][0] > 0 and r["time_to_tol"][2] >= r["time_to_tol"][0]
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4, 8, 9, 16, 17])
+@pytest.mark.parametrize("variant", [0, 2, 4, 8, 9, 16, 17, 18, 19])
 def test_fp32_kernel_variants_solve(tiny24, tiny24_oracle, variant):
     """Each non-default FP32 variant on a 3-block grid (every warp sweeps many
     slices and the ragged last one) solves the 24-bus relaxation to rel-KKT 1e-8
@@ -152,7 +152,7 @@ def test_fp32_kernel_variants_solve(tiny24, tiny24_oracle, variant):
     ws.close()
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4, 8, 9, 16, 17])
+@pytest.mark.parametrize("variant", [0, 2, 4, 8, 9, 16, 17, 18, 19])
 def test_fp32_kernel_variants_fixed_step(tiny24, variant):
     """FP32 iterates of every kernel variant on 3 blocks (each warp sweeps many
     slices and the ragged last one) equal those of the one-slice variant on the
@@ -229,5 +229,5 @@ def test_staged_variant_refuses_oversized_slices():
     ws.close()
     ws = Workspace(rp, col, val, c, l, u, q, m // 3, default_opts(max_iters=64))
     ws.solve()
-    assert ws.tuning()["fp64"]["unroll_dual"] not in (16, 17)
+    assert ws.tuning()["fp64"]["unroll_dual"] not in (16, 17, 18, 19)
     ws.close()
