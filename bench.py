@@ -83,9 +83,15 @@ def parse():
     p.add_argument("--nodes-conv-workload", default="uc200_g60_T24_slack",
                    help="node LPs solved to --nodes-conv-tol (converged node LPs/s)")
     p.add_argument("--nodes-conv-tol", type=float, default=1e-4, help="0: skip the converged node measurement")
+    p.add_argument("--nodes-rows-per-warp", type=int, default=-1, choices=[-1, 1, 2, 4],
+                   help="with --no-autotune: rows (columns) per warp of the batched sweeps")
+    p.add_argument("--nodes-grid", type=int, default=0,
+                   help="with --no-autotune: blocks of the batched sweeps (0: default)")
     p.add_argument("--host-loop", action="store_true",
                    help="launch the per-check bodies from the host instead of one CUDA graph "
                         "(same kernels; profilers cannot see kernels inside conditional graphs)")
+    p.add_argument("--no-launch-overlap", action="store_true",
+                   help="plain launches of the per-attempt kernels instead of programmatic dependent launch")
     p.add_argument("--no-autotune", action="store_true",
                    help="default launch shapes instead of timing the variants (profiler replays "
                         "distort those timings)")
@@ -157,7 +163,18 @@ def dual_kernel_name(variant: int) -> str:
     blocks per SM they are compiled for)."""
     return {0: "k_dual_pipe<float, 5>", 1: "k_dual<float, 1, 6>", 2: "k_dual<float, 2, 4>",
             4: "k_dual<float, 4, 4>", 8: "k_dual<float, 1, 8>", 9: "k_dual_pipe<float, 8>",
-            16: "k_dual_staged<float, 1>", 17: "k_dual_staged<float, 2>"}.get(variant, f"variant {variant}")
+            16: "k_dual_staged<float, 1>", 17: "k_dual_staged<float, 2>",
+            18: "k_dual_rs<float, 1>", 19: "k_dual_rs<float, 2>"}.get(variant, f"variant {variant}")
+
+
+def dual_kernel_source(variant: int) -> Path:
+    """Source file that holds the K x' kernel of a tuning variant."""
+    csrc = ROOT / "paper_2512_06715_gb300" / "csrc"
+    if variant in (16, 17):
+        return csrc / "pdhg_staged.cu"
+    if variant in (18, 19):
+        return csrc / "pdhg_rowstaged.cu"
+    return csrc / "pdhg_kernels.cu"
 
 
 def measured_peaks() -> dict:
@@ -203,11 +220,14 @@ def write_trace(out_dir: Path, tag: str, checks, r: dict, extra: dict):
     and a markdown table of about 40 evenly spaced checks plus every restart."""
     out_dir.mkdir(parents=True, exist_ok=True)
     np.save(out_dir / f"trace_{tag}.npy", checks)
-    lines = [f"# Per-check trace: {tag}", "",
+    lines = [f"# Per-check trace: {tag}", "", "Command (GB300, one GPU):", "```",
+             "python " + " ".join(sys.argv), "```", "",
              f"Options beyond the defaults: {extra or 'none'}.  Final status {r['status_name']}, "
              f"rel-KKT {r['rel_kkt']:.3e}, {r['iterations']} attempts, {r['restarts']} restarts, "
              f"{r['ir_rounds']} refinement rounds, primal weight {r['omega']:.4g}; seconds to 1e-4/1e-6/1e-8: "
              f"{[round(t, 2) for t in r['time_to_tol']]}.", "",
+             "rel_p, rel_d and rel_gap are those of the current iterate; the solver returns the better of the "
+             "current and the average candidate.", "",
              "| attempts | restart (to avg) | omega after | rel-KKT current / average | rel_p | rel_d | rel_gap |",
              "|---|---|---|---|---|---|---|"]
     if len(checks):
@@ -346,9 +366,12 @@ def node_throughput(args, dev, stream, pdhg, world=1, rank=0, workload_name=None
     converged = tol > 0
     kw = dict(precision="mixed", host_loop=int(args.host_loop), autotune=int(not args.no_autotune))
     if converged:
-        o = pdhg.default_opts(tol=tol, max_iters=10**9, time_limit_s=args.nodes_cap, **kw)
+        lim = dict(tol=tol, max_iters=10**9, time_limit_s=args.nodes_cap)
     else:
-        o = pdhg.default_opts(tol=1e-12, max_iters=args.nodes_attempts, time_limit_s=600.0, **kw)
+        lim = dict(tol=1e-12, max_iters=args.nodes_attempts, time_limit_s=600.0)
+    o = pdhg.default_opts(**lim, **kw)
+    # the batched sweeps' fixed shape (read only with --no-autotune)
+    ob = pdhg.default_opts(**lim, **kw, kernel_variant=args.nodes_rows_per_warp, kernel_grid=args.nodes_grid)
 
     def event_time(fn):
         torch.cuda.synchronize()
@@ -365,7 +388,7 @@ def node_throughput(args, dev, stream, pdhg, world=1, rank=0, workload_name=None
     if stop > start:
         l_b = torch.as_tensor(l_np[start:stop], device=dev)
         u_b = torch.as_tensor(u_np[start:stop], device=dev)
-        wb = pdhg.Workspace.from_instance(inst, o, device=dev)
+        wb = pdhg.Workspace.from_instance(inst, ob, device=dev)
         if not converged:
             wb.solve_batched(l_b, u_b, want_y=False)  # allocations, graph
         tb, (_, _, rb) = event_time(lambda: wb.solve_batched(l_b, u_b, want_y=False))
@@ -440,7 +463,8 @@ def run_ours(args):
     def opts(prec, attempts, tol=1e-8, tl=600.0):
         return pdhg.default_opts(precision=prec, max_iters=attempts, tol=tol, time_limit_s=tl,
                                  host_loop=int(args.host_loop), autotune=int(not args.no_autotune),
-                                 kernel_variant=args.kernel_variant, kernel_grid=args.kernel_grid)
+                                 kernel_variant=args.kernel_variant, kernel_grid=args.kernel_grid,
+                                 launch_overlap=int(not args.no_launch_overlap))
 
     ws = pdhg.Workspace.from_instance(inst, opts("mixed", args.attempts), device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
@@ -490,8 +514,9 @@ def run_ours(args):
     tk = ws.time_kernels(pdhg.PREC_MIXED, reps=20)
     achieved = tk["bytes_dual"] / (tk["ms_dual"] * 1e-3) / 1e9
     peaks = measured_peaks()
-    kname = dual_kernel_name(ws.tuning()["fp32"]["unroll_dual"])
-    traffic = dram_traffic_record(ROOT / "paper_2512_06715_gb300" / "csrc" / "pdhg_kernels.cu", kname)
+    dvar = ws.tuning()["fp32"]["unroll_dual"]
+    kname = dual_kernel_name(dvar)
+    traffic = dram_traffic_record(dual_kernel_source(dvar), kname)
     roofline = {"bound": "hbm", "kernel": kname + " (K x' + projected dual step)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (burst)",
@@ -521,7 +546,10 @@ def run_ours(args):
     e1.synchronize()
     e2e_s = e0.elapsed_time(e1) * 1e-3
     e2e = {"value": world * e_att * (d32 + a32) / e2e_s / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "note": "each step copies the LP's values (val, c, l, u, q) from pinned host memory, solves, and "
+                   "copies x, y back; the workspace (sliced-ELL layout of the sparsity pattern, device "
+                   "buffers, CUDA graph) is built once before the timed region"}
 
     # time to tolerance: the large LP in both precisions (capped), the small one to 1e-8
     ttt = {}
@@ -531,7 +559,8 @@ def run_ours(args):
         for kv in args.ttt_opt:
             k, v = kv.split("=")
             extra[k] = float(v) if any(ch in v for ch in ".e") else int(v)
-        for prec, cap in (("mixed", args.ttt_limit), ("fp64", args.ttt_limit_fp64)):
+        arms = [("mixed", args.ttt_limit)] + ([("fp64", args.ttt_limit_fp64)] if args.ttt_limit_fp64 > 0 else [])
+        for prec, cap in arms:
             ws.set_opts(precision=pdhg.PREC_MIXED if prec == "mixed" else pdhg.PREC_FP64,
                         max_iters=10**9, tol=1e-8, time_limit_s=cap, trace=int(bool(args.ttt_trace)), **extra)
             x, y, r = ws.solve()
@@ -546,6 +575,9 @@ def run_ours(args):
                          "ir_rounds": r["ir_rounds"], "primal_obj": r["primal_obj"]}
         ratios = {}
         for i, t in enumerate(("1e-4", "1e-6", "1e-8")):
+            if "fp64" not in ttt:
+                ratios[t] = None
+                continue
             a_m, a_f = ttt["mixed"]["seconds_to_1e-4_1e-6_1e-8"][i], ttt["fp64"]["seconds_to_1e-4_1e-6_1e-8"][i]
             ratios[t] = (a_f / a_m) if (a_m > 0 and a_f > 0) else None
         ttt["fp64_over_mixed_seconds"] = ratios
@@ -597,6 +629,7 @@ def run_ours(args):
             "roofline": roofline,
             "gpu_launches": launches,
             "kernel_tuning": ws.tuning(),
+            "launch_overlap": bool(r_mixed.get("launch_overlap", 0)),
             "e2e": e2e,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -118,10 +118,13 @@ typedef struct pdhg_opts {
                                0, 1, 2, 4, 8, 9, 16-19: that variant of both
                                per-attempt kernels, as reported by pdhg_get_tuning,
                                with the default grid; read at the first solve of
-                               each precision; default -1                          */
+                               each precision; batched solves with autotune 0: 1, 2
+                               or 4 rows (columns) per warp of both sweeps (4 for
+                               any other value); default -1                        */
   int32_t kernel_grid;      /* > 0: blocks of both per-attempt kernels, overriding the
                                autotuner's grid; small grids make each warp sweep
-                               many slices; 0: default or autotuned; default 0       */
+                               many slices; batched solves with autotune 0: blocks
+                               of both sweeps; 0: default or autotuned; default 0    */
   double infeas_tol;        /* infeasibility detection (Applegate et al.'s certificates
                                from iterate differences, the detection of the PDLP
                                method cited in Sec. II.E): at every check the
@@ -146,6 +149,13 @@ typedef struct pdhg_opts {
                                iterate stays a small correction and the per-attempt
                                changes keep FP32 resolution (0: only at the target);
                                default 16                                           */
+  int32_t launch_overlap;   /* 1: the per-attempt kernels (variants 0-9) are launched
+                               with programmatic dependent launch, so each one reads
+                               its first matrix entries while the previous kernel
+                               finishes; results are identical either way.  If the
+                               CUDA graph cannot be built with it, the library builds
+                               it without (pdhg_result.launch_overlap reports which);
+                               default 1                                            */
 } pdhg_opts;
 
 /* Outcome of one solve (host struct written by the library). */
@@ -167,7 +177,9 @@ typedef struct pdhg_result {
   int32_t returned_average;    /* 1: the last round's returned candidate was the
                                   step-weighted average since the last restart,
                                   0: the current iterate                       */
-  int32_t reserved;
+  int32_t launch_overlap;      /* 1: the per-attempt kernels ran with programmatic
+                                  dependent launch (opts.launch_overlap and accepted
+                                  by the driver), 0: plain launches             */
 } pdhg_result;
 
 /* Fill *o with the defaults listed above. */

@@ -139,6 +139,7 @@ struct IterArgs {
   int32_t kchunks2_n, tchunks2_n;
   unsigned long long cond;  // cudaGraphConditionalHandle
   int32_t in_graph;
+  int32_t overlap;  // 1: per-attempt kernels launched with programmatic dependent launch
   // FP64 data of the KKT evaluation
   SellView<double> K64, KT64;
   const double* q_res;  // q^ (FP64)
@@ -305,6 +306,18 @@ __device__ __forceinline__ double step_power(int64_t k1, double e) {
 __device__ __forceinline__ double fp32_step_cap(double omega) {
   return 1e30 / fmax(omega, 1.0 / omega);
 }
+
+// Programmatic dependent launch (sm_90 and later).  A per-attempt kernel lets
+// the next kernel in the stream start as soon as all of its own blocks are
+// running (launch_dependents); the next kernel reads only the matrix (slice
+// offsets, columns, values: constant for the whole solve) before
+// griddepcontrol.wait, which returns once every earlier grid has finished and
+// its writes are visible.  Both instructions are no-ops for a kernel launched
+// without the attribute.
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;

@@ -91,6 +91,7 @@ struct Tune {
 struct Workspace {
   int device = 0;
   int num_sms = 0;
+  bool overlap_refused = false;  // graph built without programmatic dependent launch
   pdhg_problem prob{};
   pdhg_opts opts{};
   int64_t n = 0, m = 0, m_eq = 0, nnz = 0;

@@ -103,6 +103,7 @@ IterArgs<T> make_args(Workspace* w) {
   a.tchunks2_n = w->KT.nchunks2;
   a.cond = 0;
   a.in_graph = 0;
+  a.overlap = (w->opts.launch_overlap && !w->overlap_refused) ? 1 : 0;
   a.K64 = w->K.v64();
   a.KT64 = w->KT.v64();
   a.q_res = w->q_h;
@@ -268,9 +269,28 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
 }
 
 template <class T>
+static int build_graph_once(Workspace* w);
+
+// The solve graph; built with programmatic dependent launches of the
+// per-attempt kernels when enabled, and once more without them if the driver
+// refuses that graph.
+template <class T>
 static int build_graph(Workspace* w) {
   const int pi = sizeof(T) == 8 ? 0 : 1;
   if (w->graph_exec[pi]) return PDHG_OK;
+  int rc = build_graph_once<T>(w);
+  if (rc != PDHG_OK && w->opts.launch_overlap && !w->overlap_refused) {
+    cudaGetLastError();
+    w->overlap_refused = true;
+    g_err.clear();
+    rc = build_graph_once<T>(w);
+  }
+  return rc;
+}
+
+template <class T>
+static int build_graph_once(Workspace* w) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle h;
@@ -333,6 +353,8 @@ static int validate_opts(const pdhg_opts* o) {
     return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8, 9, 16, 17, 18 or 19");
   if (o->ir_fold_checks < 0)
     return fail(PDHG_ERR_INVALID_ARG, "opts: ir_fold_checks must be >= 0");
+  if (o->launch_overlap != 0 && o->launch_overlap != 1)
+    return fail(PDHG_ERR_INVALID_ARG, "opts: launch_overlap must be 0 or 1");
   if (!(o->infeas_tol >= 0.0))
     return fail(PDHG_ERR_INVALID_ARG, "opts: infeas_tol must be >= 0");
   if (o->kernel_grid < 0 || o->kernel_grid > kMaxBlocks)
@@ -544,6 +566,7 @@ static int solve_impl(Workspace* w, double* x_out, double* y_out, pdhg_result* r
     res->omega = h.omega;
     res->kernel_launches = launches;
     res->returned_average = h.best_is_avg;
+    res->launch_overlap = (w->opts.launch_overlap && !w->overlap_refused) ? 1 : 0;
   }
   w->solved = true;
   return h.numeric ? fail(PDHG_ERR_NUMERIC, "NaN/Inf met in a KKT evaluation") : PDHG_OK;
@@ -585,6 +608,7 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->kernel_grid = 0;
   o->infeas_tol = 1e-8;
   o->ir_fold_checks = 16;
+  o->launch_overlap = 1;
   return PDHG_OK;
 }
 

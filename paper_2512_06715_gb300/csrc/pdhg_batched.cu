@@ -1318,7 +1318,14 @@ template <int BP>
 int autotune_batched(Workspace* w, Batched* bt, const BArgs<BP>& a, int B, const double* l_b,
                      const double* u_b, cudaStream_t s) {
   bt->tuned = true;
-  if (!w->opts.autotune) return PDHG_OK;
+  if (!w->opts.autotune) {
+    // fixed shape: kernel_variant 1, 2 or 4 sets R of both sweeps, kernel_grid
+    // their blocks (both grid-stride loops; partials hold kMaxBlocks blocks)
+    const int kv = w->opts.kernel_variant;
+    if (kv == 1 || kv == 2 || kv == 4) bt->rw_dual = bt->rw_adj = kv;
+    if (w->opts.kernel_grid > 0) bt->grid_rows = bt->grid_cols = std::min(w->opts.kernel_grid, kMaxBlocks);
+    return PDHG_OK;
+  }
   const char* log_env = std::getenv("UCPDHG_TUNE_LOG");
   const bool log = log_env && log_env[0] == '1';
   batched_start<BP>(w, bt, a, B, l_b, u_b, s);

@@ -118,6 +118,13 @@ __device__ __forceinline__ T sell_dot(const SellView<T>& A, int s, int lane, con
 
 template <class T, int U, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_dual(IterArgs<T> a) {
+  grid_launch_dependents();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  int ob[U + 1];
+  slice_offsets<T, U>(a.K, gw * U, ob);  // matrix only: before the previous kernel ends
+  grid_wait_prior();
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -130,14 +137,9 @@ __global__ void __launch_bounds__(kBlock, MINB) k_dual(IterArgs<T> a) {
   const T* __restrict__ xc = a.x[p];
   const T* __restrict__ yc = a.y[p];
   T* __restrict__ yn = a.y[1 - p];
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * kBlock) >> 5;
   // partials in the iterate precision up to the block totals (FP64
   // throughput on this GPU is ~1/60 of FP32); the step rule is a heuristic
   T acc_dy2 = 0, acc_int = 0;
-  int ob[U + 1];
-  slice_offsets<T, U>(a.K, gw * U, ob);
   for (int s0 = gw * U; s0 < a.K.nslices; s0 += nw * U) {
     int nb[U + 1];
     slice_offsets<T, U>(a.K, s0 + nw * U, nb);  // next group, one iteration ahead
@@ -201,6 +203,13 @@ __global__ void __launch_bounds__(kBlock, MINB) k_dual(IterArgs<T> a) {
 
 template <class T, int U, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_adjoint(IterArgs<T> a) {
+  grid_launch_dependents();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  int ob[U + 1];
+  slice_offsets<T, U>(a.KT, gw * U, ob);  // matrix only: before the previous kernel ends
+  grid_wait_prior();
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -213,12 +222,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_adjoint(IterArgs<T> a) {
   const T* __restrict__ xc = a.x[p];
   T* __restrict__ kty = a.KTy[p];
   T* __restrict__ xn = a.x[1 - p];
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * kBlock) >> 5;
   T acc_dx2 = 0;
-  int ob[U + 1];
-  if (acc_last) slice_offsets<T, U>(a.KT, gw * U, ob);
   for (int s0 = gw * U; s0 < a.KT.nslices; s0 += nw * U) {
     int nb[U + 1];
     if (acc_last) slice_offsets<T, U>(a.KT, s0 + nw * U, nb);  // one iteration ahead
@@ -330,6 +334,20 @@ __device__ __forceinline__ void staged_dot(const SellView<T>& A, const SliceStag
 
 template <class T, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_dual_pipe(IterArgs<T> a) {
+  grid_launch_dependents();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  const int ns = a.K.nslices;
+  // matrix only before the previous kernel ends: the warp's first slice
+  // (entries) and the offsets of its second
+  SliceStage<T> cur;
+  {
+    const int s = min(gw, ns);
+    stage_slice<T>(a.K, __ldg(a.K.off + s), __ldg(a.K.off + min(s + 1, ns)), lane, cur);
+  }
+  int nb0 = __ldg(a.K.off + min(gw + nw, ns)), nb1 = __ldg(a.K.off + min(gw + nw + 1, ns));
+  grid_wait_prior();
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -341,14 +359,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_dual_pipe(IterArgs<T> a) {
   const T* __restrict__ xc = a.x[p];
   const T* __restrict__ yc = a.y[p];
   T* __restrict__ yn = a.y[1 - p];
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * kBlock) >> 5;
-  const int ns = a.K.nslices;
   T acc_dy2 = 0, acc_int = 0;
   constexpr bool kStored = StoresKx<T>::value;
-  // stage the warp's first slice; offsets of the second
-  SliceStage<T> cur;
   T yo, qi, lo, yb, kxo;
   auto row_ops = [&](int s, T& y0, T& q0, T& l0, T& b0, T& k0) {
     const int i = s * kSlice + lane;
@@ -361,12 +373,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_dual_pipe(IterArgs<T> a) {
       if (kStored) k0 = a.Kx[p][i];
     }
   };
-  {
-    const int s = min(gw, ns);
-    stage_slice<T>(a.K, __ldg(a.K.off + s), __ldg(a.K.off + min(s + 1, ns)), lane, cur);
-    row_ops(gw, yo, qi, lo, yb, kxo);
-  }
-  int nb0 = __ldg(a.K.off + min(gw + nw, ns)), nb1 = __ldg(a.K.off + min(gw + nw + 1, ns));
+  row_ops(gw, yo, qi, lo, yb, kxo);
   for (int s = gw; s < ns; s += nw) {
     // next slice: entries and row operands; offsets two slices ahead
     SliceStage<T> nxt;
@@ -416,6 +423,20 @@ __global__ void __launch_bounds__(kBlock, MINB) k_dual_pipe(IterArgs<T> a) {
 
 template <class T, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_adjoint_pipe(IterArgs<T> a) {
+  grid_launch_dependents();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * kBlock) >> 5;
+  const int ns = a.KT.nslices;
+  // matrix only before the previous kernel ends (used only if the step it
+  // decides is accepted)
+  SliceStage<T> cur;
+  {
+    const int s = min(gw, ns);
+    stage_slice<T>(a.KT, __ldg(a.KT.off + s), __ldg(a.KT.off + min(s + 1, ns)), lane, cur);
+  }
+  int nb0 = __ldg(a.KT.off + min(gw + nw, ns)), nb1 = __ldg(a.KT.off + min(gw + nw + 1, ns));
+  grid_wait_prior();
   DevState* st = a.st;
   if (st->done) return;
   const int p = st->par;
@@ -428,10 +449,6 @@ __global__ void __launch_bounds__(kBlock, MINB) k_adjoint_pipe(IterArgs<T> a) {
   const T* __restrict__ xc = a.x[p];
   T* __restrict__ kty = a.KTy[p];
   T* __restrict__ xn = a.x[1 - p];
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * kBlock) >> 5;
-  const int ns = a.KT.nslices;
   T acc_dx2 = 0;
   auto col_ops = [&](int s, T& x0, T& c0, T& l0, T& u0, T& b0, T& g0) {
     const int j = s * kSlice + lane;
@@ -445,19 +462,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_adjoint_pipe(IterArgs<T> a) {
       if (!acc_last) g0 = kty[j];
     }
   };
-  SliceStage<T> cur;
-  cur.w = 0;
   T x0, cj, lj, uj, xb, g;
-  if (acc_last) {
-    const int s = min(gw, ns);
-    stage_slice<T>(a.KT, __ldg(a.KT.off + s), __ldg(a.KT.off + min(s + 1, ns)), lane, cur);
-  }
   col_ops(gw, x0, cj, lj, uj, xb, g);
-  int nb0 = 0, nb1 = 0;
-  if (acc_last) {
-    nb0 = __ldg(a.KT.off + min(gw + nw, ns));
-    nb1 = __ldg(a.KT.off + min(gw + nw + 1, ns));
-  }
   for (int s = gw; s < ns; s += nw) {
     SliceStage<T> nxt;
     nxt.w = 0;
@@ -651,35 +657,57 @@ struct MinBlocksPipe {
   static constexpr int value = sizeof(T) == 4 ? 5 : 3;
 };
 
+// One per-attempt kernel, with the programmatic-dependent-launch attribute when
+// a.overlap is set (the kernel then overlaps its matrix prologue with the end
+// of the previous kernel in the stream or graph).
+template <class T>
+static void launch_iter(void (*k)(IterArgs<T>), const IterArgs<T>& a, int grid, cudaStream_t s) {
+  if (!a.overlap) {
+    k<<<grid, kBlock, 0, s>>>(a);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, a);
+}
+
 template <class T>
 void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
-    case 0: k_dual_pipe<T, MinBlocksPipe<T>::value><<<grid, kBlock, 0, s>>>(a); break;
-    case 2: k_dual<T, 2, MinBlocks<T, 2>::value><<<grid, kBlock, 0, s>>>(a); break;
-    case 4: k_dual<T, 4, MinBlocks<T, 4>::value><<<grid, kBlock, 0, s>>>(a); break;
-    case 8: k_dual<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
-    case 9: k_dual_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
+    case 0: launch_iter<T>(k_dual_pipe<T, MinBlocksPipe<T>::value>, a, grid, s); break;
+    case 2: launch_iter<T>(k_dual<T, 2, MinBlocks<T, 2>::value>, a, grid, s); break;
+    case 4: launch_iter<T>(k_dual<T, 4, MinBlocks<T, 4>::value>, a, grid, s); break;
+    case 8: launch_iter<T>(k_dual<T, 1, 8>, a, grid, s); break;
+    case 9: launch_iter<T>(k_dual_pipe<T, 8>, a, grid, s); break;
     case 16: launch_dual_staged<T>(a, grid, s, 1); break;
     case 17: launch_dual_staged<T>(a, grid, s, 2); break;
     case 18: launch_dual_rowstaged<T>(a, grid, s, 1); break;
     case 19: launch_dual_rowstaged<T>(a, grid, s, 2); break;
-    default: k_dual<T, 1, MinBlocks<T, 1>::value><<<grid, kBlock, 0, s>>>(a); break;
+    default: launch_iter<T>(k_dual<T, 1, MinBlocks<T, 1>::value>, a, grid, s); break;
   }
 }
 
 template <class T>
 void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
   switch (unroll) {
-    case 0: k_adjoint_pipe<T, MinBlocksPipe<T>::value><<<grid, kBlock, 0, s>>>(a); break;
-    case 2: k_adjoint<T, 2, MinBlocks<T, 2>::value><<<grid, kBlock, 0, s>>>(a); break;
-    case 4: k_adjoint<T, 4, MinBlocks<T, 4>::value><<<grid, kBlock, 0, s>>>(a); break;
-    case 8: k_adjoint<T, 1, 8><<<grid, kBlock, 0, s>>>(a); break;
-    case 9: k_adjoint_pipe<T, 8><<<grid, kBlock, 0, s>>>(a); break;
+    case 0: launch_iter<T>(k_adjoint_pipe<T, MinBlocksPipe<T>::value>, a, grid, s); break;
+    case 2: launch_iter<T>(k_adjoint<T, 2, MinBlocks<T, 2>::value>, a, grid, s); break;
+    case 4: launch_iter<T>(k_adjoint<T, 4, MinBlocks<T, 4>::value>, a, grid, s); break;
+    case 8: launch_iter<T>(k_adjoint<T, 1, 8>, a, grid, s); break;
+    case 9: launch_iter<T>(k_adjoint_pipe<T, 8>, a, grid, s); break;
     case 16: launch_adjoint_staged<T>(a, grid, s, 1); break;
     case 17: launch_adjoint_staged<T>(a, grid, s, 2); break;
     case 18: launch_adjoint_rowstaged<T>(a, grid, s, 1); break;
     case 19: launch_adjoint_rowstaged<T>(a, grid, s, 2); break;
-    default: k_adjoint<T, 1, MinBlocks<T, 1>::value><<<grid, kBlock, 0, s>>>(a); break;
+    default: launch_iter<T>(k_adjoint<T, 1, MinBlocks<T, 1>::value>, a, grid, s); break;
   }
 }
 

@@ -38,7 +38,7 @@ class pdhg_opts(C.Structure):
                 ("bound_obj_rescale", C.c_int32), ("artificial_total", C.c_int32),
                 ("host_loop", C.c_int32), ("autotune", C.c_int32), ("cancel_flag", C.c_void_p),
                 ("kernel_variant", C.c_int32), ("kernel_grid", C.c_int32), ("infeas_tol", C.c_double),
-                ("ir_fold_checks", C.c_int32)]
+                ("ir_fold_checks", C.c_int32), ("launch_overlap", C.c_int32)]
 
 
 class pdhg_result(C.Structure):
@@ -48,7 +48,7 @@ class pdhg_result(C.Structure):
                 ("rel_kkt", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("solve_seconds", C.c_double), ("time_to_tol", C.c_double * 3),
                 ("iters_to_tol", C.c_int64 * 3), ("eta", C.c_double), ("omega", C.c_double),
-                ("kernel_launches", C.c_int64), ("returned_average", C.c_int32), ("reserved", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("returned_average", C.c_int32), ("launch_overlap", C.c_int32)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -231,3 +231,28 @@ def test_staged_variant_refuses_oversized_slices():
     ws.solve()
     assert ws.tuning()["fp64"]["unroll_dual"] not in (16, 17, 18, 19)
     ws.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("variant,grid", [(1, 0), (0, 0), (2, 3), (0, 3)])
+def test_launch_overlap_is_bit_identical(tiny24, precision, variant, grid):
+    """Programmatic dependent launch changes only when each per-attempt kernel
+    starts reading the matrix: 1024 adaptive attempts (restarts, primal-weight
+    updates, refinement folds in mixed precision) give bitwise the same
+    iterates, decisions and counts with and without it, in the CUDA graph and
+    launched from the host."""
+    inst, _ = tiny24
+    runs = {}
+    for overlap in (1, 0):
+        for host_loop in (0, 1):
+            ws = _ws(inst, precision=precision, max_iters=1024, tol=1e-30, kernel_variant=variant,
+                     kernel_grid=grid, launch_overlap=overlap, host_loop=host_loop)
+            x, y, r = ws.solve()
+            assert r["launch_overlap"] == overlap, r
+            runs[(overlap, host_loop)] = (x.cpu().numpy(), y.cpu().numpy(), r)
+            ws.close()
+    x0, y0, r0 = runs[(0, 0)]
+    for key, (x, y, r) in runs.items():
+        assert np.array_equal(x, x0) and np.array_equal(y, y0), key
+        for k in ("iterations", "accepted", "restarts", "rel_kkt", "omega", "eta", "ir_rounds"):
+            assert r[k] == r0[k], (key, k, r[k], r0[k])

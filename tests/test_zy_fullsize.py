@@ -13,7 +13,10 @@ the autotuned launch configuration the bench uses.
   relative.
 - The FP64 rel-KKT the GPU reports for its returned point, after a short adaptive
   solve in mixed precision, equals the oracle's recomputation from that point (a
-  property of the check reductions that holds at any size)."""
+  property of the check reductions that holds at any size).
+- Programmatic dependent launch of the per-attempt kernels (the default) gives
+  bitwise the same iterates as plain launches over 256 adaptive attempts with
+  the two variants the autotuner picks at this size, in both precisions."""
 import numpy as np
 import pytest
 
@@ -84,3 +87,22 @@ def test_reported_rel_kkt_full_size(full):
     assert np.isfinite(chk.rel_kkt)
     assert abs(chk.rel_kkt - r["rel_kkt"]) <= 1e-2 * r["rel_kkt"] + 1e-12, (chk.rel_kkt, r["rel_kkt"])
     assert abs(chk.primal_obj - r["primal_obj"]) <= 1e-8 * max(1.0, abs(chk.primal_obj))
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_launch_overlap_bit_identical_full_size(full, precision, variant):
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst = full[0]
+    out = []
+    for overlap in (1, 0):
+        ws = Workspace.from_instance(inst, default_opts(precision=precision, max_iters=256, tol=1e-30,
+                                                        time_limit_s=120.0, kernel_variant=variant,
+                                                        launch_overlap=overlap))
+        x, y, r = ws.solve()
+        assert r["launch_overlap"] == overlap
+        out.append((x.cpu().numpy(), y.cpu().numpy(), r))
+        ws.close()
+    (x1, y1, r1), (x0, y0, r0) = out
+    assert np.array_equal(x1, x0) and np.array_equal(y1, y0)
+    assert (r1["iterations"], r1["accepted"], r1["restarts"]) == (r0["iterations"], r0["accepted"], r0["restarts"])
