@@ -90,8 +90,8 @@ def parse():
     p.add_argument("--host-loop", action="store_true",
                    help="launch the per-check bodies from the host instead of one CUDA graph "
                         "(same kernels; profilers cannot see kernels inside conditional graphs)")
-    p.add_argument("--no-launch-overlap", action="store_true",
-                   help="plain launches of the per-attempt kernels instead of programmatic dependent launch")
+    p.add_argument("--launch-overlap", action="store_true",
+                   help="programmatic dependent launch of the per-attempt kernels (default: plain launches)")
     p.add_argument("--no-autotune", action="store_true",
                    help="default launch shapes instead of timing the variants (profiler replays "
                         "distort those timings)")
@@ -464,7 +464,7 @@ def run_ours(args):
         return pdhg.default_opts(precision=prec, max_iters=attempts, tol=tol, time_limit_s=tl,
                                  host_loop=int(args.host_loop), autotune=int(not args.no_autotune),
                                  kernel_variant=args.kernel_variant, kernel_grid=args.kernel_grid,
-                                 launch_overlap=int(not args.no_launch_overlap))
+                                 launch_overlap=int(args.launch_overlap))
 
     ws = pdhg.Workspace.from_instance(inst, opts("mixed", args.attempts), device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2

@@ -154,8 +154,11 @@ typedef struct pdhg_opts {
                                its first matrix entries while the previous kernel
                                finishes; results are identical either way.  If the
                                CUDA graph cannot be built with it, the library builds
-                               it without (pdhg_result.launch_overlap reports which);
-                               default 1                                            */
+                               it without (pdhg_result.launch_overlap reports which).
+                               Measured within 1-2% of plain launches on GB300 (the
+                               per-kernel floor is the chain of dependent memory
+                               round trips inside each kernel, not the launch);
+                               default 0                                            */
 } pdhg_opts;
 
 /* Outcome of one solve (host struct written by the library). */

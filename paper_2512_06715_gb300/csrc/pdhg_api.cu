@@ -608,7 +608,7 @@ extern "C" int pdhg_opts_default(pdhg_opts* o) {
   o->kernel_grid = 0;
   o->infeas_tol = 1e-8;
   o->ir_fold_checks = 16;
-  o->launch_overlap = 1;
+  o->launch_overlap = 0;
   return PDHG_OK;
 }
 

@@ -14,7 +14,7 @@ the autotuned launch configuration the bench uses.
 - The FP64 rel-KKT the GPU reports for its returned point, after a short adaptive
   solve in mixed precision, equals the oracle's recomputation from that point (a
   property of the check reductions that holds at any size).
-- Programmatic dependent launch of the per-attempt kernels (the default) gives
+- Programmatic dependent launch of the per-attempt kernels (launch_overlap) gives
   bitwise the same iterates as plain launches over 256 adaptive attempts with
   the two variants the autotuner picks at this size, in both precisions."""
 import numpy as np
