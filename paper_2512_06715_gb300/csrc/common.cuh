@@ -307,6 +307,41 @@ __device__ __forceinline__ double fp32_step_cap(double omega) {
   return 1e30 / fmax(omega, 1.0 / omega);
 }
 
+// Per-attempt scalars of the step kernels, read from the device state and
+// converted by thread 0 of each block, then shared: GB300 retires FP64
+// instructions at a small fraction of its FP32 rate, so an FP64 multiply,
+// divide or conversion in every thread held every warp of a launch on the
+// FP64 pipe before its first slice.
+template <class T>
+struct DualScalars {
+  int done, p, has_pw;
+  T pw, sigma;
+};
+template <class T>
+__device__ __forceinline__ void dual_scalars(const DevState* st, DualScalars<T>& s) {
+  s.done = st->done;
+  s.p = st->par;
+  const double pw = st->pending_w;
+  s.has_pw = pw != 0.0;
+  s.pw = (T)pw;
+  s.sigma = (T)(st->eta * st->omega);
+}
+template <class T>
+struct AdjScalars {
+  int done, p, acc_last, upd_avg;
+  T wl, tau;
+};
+template <class T>
+__device__ __forceinline__ void adj_scalars(const DevState* st, AdjScalars<T>& s) {
+  s.done = st->done;
+  s.p = st->par;
+  s.acc_last = st->accepted_last;
+  const double wl = st->w_last;
+  s.upd_avg = s.acc_last && wl != 0.0;
+  s.wl = (T)wl;
+  s.tau = (T)(st->eta / st->omega);
+}
+
 // Programmatic dependent launch (sm_90 and later).  A per-attempt kernel lets
 // the next kernel in the stream start as soon as all of its own blocks are
 // running (launch_dependents); the next kernel reads only the matrix (slice

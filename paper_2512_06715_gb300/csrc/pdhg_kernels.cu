@@ -126,13 +126,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_dual(IterArgs<T> a) {
   slice_offsets<T, U>(a.K, gw * U, ob);  // matrix only: before the previous kernel ends
   grid_wait_prior();
   DevState* st = a.st;
-  if (st->done) return;
-  const int p = st->par;
-  const double pw = st->pending_w;
-  // scalars converted once: a per-row FP64 compare or cast costs an FP64-pipe slot
-  const bool has_pw = pw != 0.0;
-  const T pwT = (T)pw;
-  const T sigma = (T)(st->eta * st->omega);
+  __shared__ DualScalars<T> sc;
+  if (threadIdx.x == 0) dual_scalars<T>(st, sc);
+  __syncthreads();
+  if (sc.done) return;
+  const int p = sc.p;
+  const bool has_pw = sc.has_pw;
+  const T pwT = sc.pw;
+  const T sigma = sc.sigma;
   const T* __restrict__ xn = a.x[1 - p];
   const T* __restrict__ xc = a.x[p];
   const T* __restrict__ yc = a.y[p];
@@ -211,13 +212,15 @@ __global__ void __launch_bounds__(kBlock, MINB) k_adjoint(IterArgs<T> a) {
   slice_offsets<T, U>(a.KT, gw * U, ob);  // matrix only: before the previous kernel ends
   grid_wait_prior();
   DevState* st = a.st;
-  if (st->done) return;
-  const int p = st->par;
-  const int acc_last = st->accepted_last;
-  const double wl = st->w_last;
-  const bool upd_avg = acc_last && wl != 0.0;
-  const T wlT = (T)wl;
-  const T tau = (T)(st->eta / st->omega);
+  __shared__ AdjScalars<T> sc;
+  if (threadIdx.x == 0) adj_scalars<T>(st, sc);
+  __syncthreads();
+  if (sc.done) return;
+  const int p = sc.p;
+  const int acc_last = sc.acc_last;
+  const bool upd_avg = sc.upd_avg;
+  const T wlT = sc.wl;
+  const T tau = sc.tau;
   const T* __restrict__ yc = a.y[p];
   const T* __restrict__ xc = a.x[p];
   T* __restrict__ kty = a.KTy[p];
@@ -349,12 +352,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_dual_pipe(IterArgs<T> a) {
   int nb0 = __ldg(a.K.off + min(gw + nw, ns)), nb1 = __ldg(a.K.off + min(gw + nw + 1, ns));
   grid_wait_prior();
   DevState* st = a.st;
-  if (st->done) return;
-  const int p = st->par;
-  const double pw = st->pending_w;
-  const bool has_pw = pw != 0.0;
-  const T pwT = (T)pw;
-  const T sigma = (T)(st->eta * st->omega);
+  __shared__ DualScalars<T> sc;
+  if (threadIdx.x == 0) dual_scalars<T>(st, sc);
+  __syncthreads();
+  if (sc.done) return;
+  const int p = sc.p;
+  const bool has_pw = sc.has_pw;
+  const T pwT = sc.pw;
+  const T sigma = sc.sigma;
   const T* __restrict__ xn = a.x[1 - p];
   const T* __restrict__ xc = a.x[p];
   const T* __restrict__ yc = a.y[p];
@@ -438,13 +443,15 @@ __global__ void __launch_bounds__(kBlock, MINB) k_adjoint_pipe(IterArgs<T> a) {
   int nb0 = __ldg(a.KT.off + min(gw + nw, ns)), nb1 = __ldg(a.KT.off + min(gw + nw + 1, ns));
   grid_wait_prior();
   DevState* st = a.st;
-  if (st->done) return;
-  const int p = st->par;
-  const int acc_last = st->accepted_last;
-  const double wl = st->w_last;
-  const bool upd_avg = acc_last && wl != 0.0;
-  const T wlT = (T)wl;
-  const T tau = (T)(st->eta / st->omega);
+  __shared__ AdjScalars<T> sc;
+  if (threadIdx.x == 0) adj_scalars<T>(st, sc);
+  __syncthreads();
+  if (sc.done) return;
+  const int p = sc.p;
+  const int acc_last = sc.acc_last;
+  const bool upd_avg = sc.upd_avg;
+  const T wlT = sc.wl;
+  const T tau = sc.tau;
   const T* __restrict__ yc = a.y[p];
   const T* __restrict__ xc = a.x[p];
   T* __restrict__ kty = a.KTy[p];

@@ -67,15 +67,17 @@ __device__ __forceinline__ void issue_rows(const SellView<T>& A, const int32_t* 
 template <class T, int P>
 __global__ void __launch_bounds__(kBlock) k_dual_rs(IterArgs<T> a) {
   DevState* st = a.st;
-  if (st->done) return;
+  __shared__ DualScalars<T> sc;
+  if (threadIdx.x == 0) dual_scalars<T>(st, sc);
+  __syncthreads();
+  if (sc.done) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   RowStage<T, 4> sm(smem_raw);
   __shared__ int s_abort;
-  const int p = st->par;
-  const double pw = st->pending_w;
-  const bool has_pw = pw != 0.0;
-  const T pwT = (T)pw;
-  const T sigma = (T)(st->eta * st->omega);
+  const int p = sc.p;
+  const bool has_pw = sc.has_pw;
+  const T pwT = sc.pw;
+  const T sigma = sc.sigma;
   const T* __restrict__ xn = a.x[1 - p];
   const T* __restrict__ xc = a.x[p];
   T* __restrict__ yn = a.y[1 - p];
@@ -141,16 +143,18 @@ __global__ void __launch_bounds__(kBlock) k_dual_rs(IterArgs<T> a) {
 template <class T, int P>
 __global__ void __launch_bounds__(kBlock) k_adjoint_rs(IterArgs<T> a) {
   DevState* st = a.st;
-  if (st->done) return;
+  __shared__ AdjScalars<T> sc;
+  if (threadIdx.x == 0) adj_scalars<T>(st, sc);
+  __syncthreads();
+  if (sc.done) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   RowStage<T, 5> sm(smem_raw);
   __shared__ int s_abort;
-  const int p = st->par;
-  const int acc_last = st->accepted_last;
-  const double wl = st->w_last;
-  const bool upd_avg = acc_last && wl != 0.0;
-  const T wlT = (T)wl;
-  const T tau = (T)(st->eta / st->omega);
+  const int p = sc.p;
+  const int acc_last = sc.acc_last;
+  const bool upd_avg = sc.upd_avg;
+  const T wlT = sc.wl;
+  const T tau = sc.tau;
   const T* __restrict__ yc = a.y[p];
   const T* __restrict__ xc = a.x[p];
   T* __restrict__ kty = a.KTy[p];
