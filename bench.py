@@ -164,7 +164,8 @@ def dual_kernel_name(variant: int) -> str:
     return {0: "k_dual_pipe<float, 5>", 1: "k_dual<float, 1, 6>", 2: "k_dual<float, 2, 4>",
             4: "k_dual<float, 4, 4>", 8: "k_dual<float, 1, 8>", 9: "k_dual_pipe<float, 8>",
             16: "k_dual_staged<float, 1>", 17: "k_dual_staged<float, 2>",
-            18: "k_dual_rs<float, 1>", 19: "k_dual_rs<float, 2>"}.get(variant, f"variant {variant}")
+            18: "k_dual_rs<float, 1>", 19: "k_dual_rs<float, 2>",
+            20: "k_dual_ring<float, 3>", 21: "k_dual_ring<float, 4>"}.get(variant, f"variant {variant}")
 
 
 def dual_kernel_source(variant: int) -> Path:
@@ -174,6 +175,8 @@ def dual_kernel_source(variant: int) -> Path:
         return csrc / "pdhg_staged.cu"
     if variant in (18, 19):
         return csrc / "pdhg_rowstaged.cu"
+    if variant in (20, 21):
+        return csrc / "pdhg_ring.cu"
     return csrc / "pdhg_kernels.cu"
 
 

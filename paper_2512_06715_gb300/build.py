@@ -34,6 +34,7 @@ CUDA_SOURCES = [
     "pdhg_noalloc.cu",
     "pdhg_staged.cu",
     "pdhg_rowstaged.cu",
+    "pdhg_ring.cu",
 ]
 
 

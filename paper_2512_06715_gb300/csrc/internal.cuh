@@ -167,6 +167,12 @@ void launch_dual_rowstaged(const IterArgs<T>& a, int grid, cudaStream_t s, int p
 template <class T>
 void launch_adjoint_rowstaged(const IterArgs<T>& a, int grid, cudaStream_t s, int pair);
 int rowstaged_setup();
+// pdhg_ring.cu: per-warp rings of asynchronous copies (3 or 4 slots)
+template <class T>
+void launch_dual_ring(const IterArgs<T>& a, int grid, cudaStream_t s, int slots);
+template <class T>
+void launch_adjoint_ring(const IterArgs<T>& a, int grid, cudaStream_t s, int slots);
+int ring_setup();
 // chunks of consecutive slices with at most max_entries entries and max_slices
 // slices each; false if a single slice is larger
 bool build_chunks(const std::vector<int32_t>& off, std::vector<int32_t>* chunks, int max_entries,

@@ -199,6 +199,8 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
         (w->K.nchunks2 == 0 || w->KT.nchunks2 == 0 || rowstaged_setup() != 0))
       return fail(PDHG_ERR_UNSUPPORTED,
                   "kernel_variant 18/19: a slice exceeds the row-staged chunk size on this matrix");
+    if ((fixed_variant == 20 || fixed_variant == 21) && ring_setup() != 0)
+      return fail(PDHG_ERR_CUDA, "kernel_variant 20/21: shared-memory opt-in refused");
     if (w->opts.kernel_grid > 0) t.grid_dual = t.grid_adj = w->opts.kernel_grid;
     t.done = true;
     return PDHG_OK;
@@ -206,10 +208,11 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   // 1, 2, 4: slices a warp sweeps together; 0: one slice per warp, software
   // pipelined (the next slice's first entries and row operands load early);
   // 8, 9: the one-slice and pipelined forms limited to 32 registers (8 blocks
-  // per SM)
+  // per SM); 16-19: TMA-staged chunks; 20, 21: per-warp cp.async rings
   const bool staged = w->K.nchunks > 0 && w->KT.nchunks > 0 && staged_setup() == 0;
   const bool rowstaged = w->K.nchunks2 > 0 && w->KT.nchunks2 > 0 && rowstaged_setup() == 0;
-  const int unrolls[10] = {1, 2, 4, 0, 8, 9, 16, 17, 18, 19};
+  const bool ring = ring_setup() == 0;
+  const int unrolls[12] = {1, 2, 4, 0, 8, 9, 16, 17, 18, 19, 20, 21};
   const int bps[5] = {2, 3, 4, 6, 8};
   // UCPDHG_TUNE_LOG=1 prints every timed candidate to stderr
   const char* log_env = std::getenv("UCPDHG_TUNE_LOG");
@@ -218,10 +221,11 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
     const int nsl = which == 0 ? w->K.nslices : w->KT.nslices;
     float best = 1e30f;
     int bu = 1, bg = which == 0 ? w->grid_k : w->grid_kt;
-    for (int ui = 0; ui < 10; ++ui) {
+    for (int ui = 0; ui < 12; ++ui) {
       const int U = unrolls[ui];
       if ((U == 16 || U == 17) && !staged) continue;
       if ((U == 18 || U == 19) && !rowstaged) continue;
+      if ((U == 20 || U == 21) && !ring) continue;
       const int Us = (U == 2 || U == 4) ? U : 1;
       const int need = (nsl + kWarps * Us - 1) / (kWarps * Us);
       for (int bi = 0; bi < 5; ++bi) {
@@ -349,8 +353,9 @@ static int validate_opts(const pdhg_opts* o) {
   if (!(o->kernel_variant == -1 || o->kernel_variant == 0 || o->kernel_variant == 1 ||
         o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 8 ||
         o->kernel_variant == 9 || o->kernel_variant == 16 || o->kernel_variant == 17 ||
-        o->kernel_variant == 18 || o->kernel_variant == 19))
-    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8, 9, 16, 17, 18 or 19");
+        o->kernel_variant == 18 || o->kernel_variant == 19 || o->kernel_variant == 20 ||
+        o->kernel_variant == 21))
+    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8, 9 or 16-21");
   if (o->ir_fold_checks < 0)
     return fail(PDHG_ERR_INVALID_ARG, "opts: ir_fold_checks must be >= 0");
   if (o->launch_overlap != 0 && o->launch_overlap != 1)

@@ -650,7 +650,8 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
 // the HBM and L2 latency at the cost of the spills; 16 and 17 stage the matrix
 // in shared memory with bulk copies (pdhg_staged.cu), one or two slices per
 // warp at a time; 18 and 19 stage the row (column) operands with the matrix
-// chunk (pdhg_rowstaged.cu).
+// chunk (pdhg_rowstaged.cu); 20 and 21 keep two or three slices ahead in a
+// per-warp shared-memory ring filled by cp.async (pdhg_ring.cu).
 // Minimum resident blocks per SM that each variant is compiled for: the
 // register budget that keeps the one-slice forms at 6 (FP32) or 5 (FP64)
 // blocks per SM without spills (an unconstrained build takes ~58 registers and
@@ -698,6 +699,8 @@ void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
     case 17: launch_dual_staged<T>(a, grid, s, 2); break;
     case 18: launch_dual_rowstaged<T>(a, grid, s, 1); break;
     case 19: launch_dual_rowstaged<T>(a, grid, s, 2); break;
+    case 20: launch_dual_ring<T>(a, grid, s, 3); break;
+    case 21: launch_dual_ring<T>(a, grid, s, 4); break;
     default: launch_iter<T>(k_dual<T, 1, MinBlocks<T, 1>::value>, a, grid, s); break;
   }
 }
@@ -714,6 +717,8 @@ void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) 
     case 17: launch_adjoint_staged<T>(a, grid, s, 2); break;
     case 18: launch_adjoint_rowstaged<T>(a, grid, s, 1); break;
     case 19: launch_adjoint_rowstaged<T>(a, grid, s, 2); break;
+    case 20: launch_adjoint_ring<T>(a, grid, s, 3); break;
+    case 21: launch_adjoint_ring<T>(a, grid, s, 4); break;
     default: launch_iter<T>(k_adjoint<T, 1, MinBlocks<T, 1>::value>, a, grid, s); break;
   }
 }

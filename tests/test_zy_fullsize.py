@@ -16,7 +16,11 @@ the autotuned launch configuration the bench uses.
   property of the check reductions that holds at any size).
 - Programmatic dependent launch of the per-attempt kernels (launch_overlap) gives
   bitwise the same iterates as plain launches over 256 adaptive attempts with
-  the two variants the autotuner picks at this size, in both precisions."""
+  the two variants the autotuner picks at this size, in both precisions.
+- The cp.async-ring variants (20, 21) sum every product in the order of the
+  software-pipelined variant (0): on the same grid their iterates after 256
+  adaptive attempts agree with it to FP32 (FP64) rounding of a contraction
+  difference, with the same accept/restart decisions."""
 import numpy as np
 import pytest
 
@@ -106,3 +110,21 @@ def test_launch_overlap_bit_identical_full_size(full, precision, variant):
     (x1, y1, r1), (x0, y0, r0) = out
     assert np.array_equal(x1, x0) and np.array_equal(y1, y0)
     assert (r1["iterations"], r1["accepted"], r1["restarts"]) == (r0["iterations"], r0["accepted"], r0["restarts"])
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-12)])
+@pytest.mark.parametrize("variant", [20, 21])
+def test_ring_variants_match_pipelined_full_size(full, precision, tol, variant):
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst = full[0]
+    out = []
+    for v in (0, variant):
+        ws = Workspace.from_instance(inst, default_opts(precision=precision, max_iters=256, tol=1e-30,
+                                                        time_limit_s=120.0, kernel_variant=v, kernel_grid=912))
+        x, y, r = ws.solve()
+        out.append((x.cpu().numpy(), y.cpu().numpy(), r))
+        ws.close()
+    (x0, y0, r0), (xv, yv, rv) = out
+    assert (rv["iterations"], rv["accepted"], rv["restarts"]) == (r0["iterations"], r0["accepted"], r0["restarts"])
+    assert np.abs(xv - x0).max() <= tol * np.abs(x0).max()
+    assert np.abs(yv - y0).max() <= tol * np.abs(y0).max()
