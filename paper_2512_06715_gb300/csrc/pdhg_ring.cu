@@ -8,9 +8,10 @@
 // registers held while the copy is in flight), fills the slot of the slice R-1
 // sweeps ahead with that slice's first kRingE entries per row (columns and
 // values) and its row operands, before it computes the current slice from its
-// own slot.  Each lane copies and reads only its own elements, so the ring
-// needs no block barrier and no warp-wide wait beyond the copy group of the
-// slice it consumes.  Entries beyond kRingE (the long rows) are read directly.
+// own slot.  The copies are 16-byte pieces spread over the warp and cached in
+// L2 only; the ring needs no block barrier, only the warp's wait for the copy
+// group of the slice it consumes.  Entries beyond kRingE (the long rows) are
+// read directly.
 // Products are summed in the same order as the other variants.
 #include "internal.cuh"
 
@@ -23,12 +24,40 @@ __device__ __forceinline__ uint32_t ring_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-template <class T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(ring_u32(dst)), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(ring_u32(dst)), "l"(src) : "memory");
+// 16 bytes global -> shared, cached in L2 only (the streamed matrix and
+// operands do not displace the gathered iterate from L1); both addresses
+// 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(ring_u32(dst)), "l"(src) : "memory");
+}
+
+// The copies of one slice, spread over the warp in 16-byte pieces: kRingE
+// entry rows of columns and of values (128 B each for int32/FP32, 256 B for
+// FP64 values) and NR operand rows.  Every slice offset is a multiple of 32
+// entries and every vector a whole number of 32-row slices long, so each piece
+// is aligned and inside its array.  src(v) is operand row v's first element,
+// or nullptr if the row is not needed.
+template <class T, int NR, class Slot, class Src>
+__device__ __forceinline__ void issue_slice(Slot& sl, const int* col, const T* val, int ob, int w, int lane,
+                                            Src src) {
+  constexpr int EP = 16 / (int)sizeof(T);  // elements of T per piece
+  constexpr int PP = kSlice / EP;          // pieces per 32-element row of T
+#pragma unroll
+  for (int t = lane; t < kRingE * 8; t += 32) {  // columns: 8 pieces per entry row
+    const int e = t >> 3, pc = t & 7;
+    if (e < w) cp_async16(&sl.col[e][pc * 4], col + ob + e * kSlice + pc * 4);
+  }
+#pragma unroll
+  for (int t = lane; t < kRingE * PP; t += 32) {
+    const int e = t / PP, pc = t % PP;
+    if (e < w) cp_async16(&sl.val[e][pc * EP], val + ob + e * kSlice + pc * EP);
+  }
+#pragma unroll
+  for (int t = lane; t < NR * PP; t += 32) {
+    const int v = t / PP, pc = t % PP;
+    const T* p = src(v);
+    if (p) cp_async16(&sl.row[v][pc * EP], p + pc * EP);
+  }
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -93,21 +122,16 @@ __global__ void __launch_bounds__(kBlock) k_dual_ring(IterArgs<T> a) {
         sl.hdr[0] = ob;
         sl.hdr[1] = w;
       }
-      const int o0 = ob + lane;
-#pragma unroll
-      for (int e = 0; e < kRingE; ++e)
-        if (e < w) {
-          cp_async_elem<int>(&sl.col[e][lane], a.K.col + o0 + e * kSlice);
-          cp_async_elem<T>(&sl.val[e][lane], a.K.val + o0 + e * kSlice);
+      const int r0 = s * kSlice;
+      issue_slice<T, NR>(sl, a.K.col, a.K.val, ob, w, lane, [&](int v) -> const T* {
+        switch (v) {
+          case 0: return yc + r0;
+          case 1: return a.q + r0;
+          case 2: return a.ylo ? a.ylo + r0 : nullptr;
+          case 3: return has_pw ? a.ybar + r0 : nullptr;
+          default: return kStored ? kxc + r0 : nullptr;
         }
-      const int i = s * kSlice + lane;
-      if (i < a.m) {
-        cp_async_elem<T>(&sl.row[0][lane], yc + i);
-        cp_async_elem<T>(&sl.row[1][lane], a.q + i);
-        if (a.ylo && i >= a.m_eq) cp_async_elem<T>(&sl.row[2][lane], a.ylo + i);
-        if (has_pw) cp_async_elem<T>(&sl.row[3][lane], a.ybar + i);
-        if constexpr (kStored) cp_async_elem<T>(&sl.row[NR - 1][lane], kxc + i);
-      }
+      });
     }
     cp_async_commit();
   };
@@ -128,7 +152,7 @@ __global__ void __launch_bounds__(kBlock) k_dual_ring(IterArgs<T> a) {
     nb0 = __ldg(a.K.off + min(s_next, ns));
     nb1 = __ldg(a.K.off + min(s_next + 1, ns));
     cp_async_wait<R - 1>();  // this lane's copies of slice s have landed
-    __syncwarp();            // and lane 0's header is visible
+    __syncwarp();            // and every other lane's, and lane 0's header
     const Slot& sl = ring[k];
     const int o0 = sl.hdr[0] + lane, w = sl.hdr[1];
     T kx = 0, ko = 0;
@@ -217,22 +241,17 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_ring(IterArgs<T> a) {
         sl.hdr[0] = ob;
         sl.hdr[1] = w;
       }
-      const int o0 = ob + lane;
-#pragma unroll
-      for (int e = 0; e < kRingE; ++e)
-        if (e < w) {
-          cp_async_elem<int>(&sl.col[e][lane], a.KT.col + o0 + e * kSlice);
-          cp_async_elem<T>(&sl.val[e][lane], a.KT.val + o0 + e * kSlice);
+      const int r0 = s * kSlice;
+      issue_slice<T, kAdjOps>(sl, a.KT.col, a.KT.val, ob, w, lane, [&](int v) -> const T* {
+        switch (v) {
+          case 0: return xc + r0;
+          case 1: return a.c + r0;
+          case 2: return a.l + r0;
+          case 3: return a.u + r0;
+          case 4: return upd_avg ? a.xbar + r0 : nullptr;
+          default: return acc_last ? nullptr : kty + r0;
         }
-      const int j = s * kSlice + lane;
-      if (j < a.n) {
-        cp_async_elem<T>(&sl.row[0][lane], xc + j);
-        cp_async_elem<T>(&sl.row[1][lane], a.c + j);
-        cp_async_elem<T>(&sl.row[2][lane], a.l + j);
-        cp_async_elem<T>(&sl.row[3][lane], a.u + j);
-        if (upd_avg) cp_async_elem<T>(&sl.row[4][lane], a.xbar + j);
-        if (!acc_last) cp_async_elem<T>(&sl.row[5][lane], kty + j);
-      }
+      });
     }
     cp_async_commit();
   };
