@@ -213,7 +213,9 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   const bool rowstaged = w->K.nchunks2 > 0 && w->KT.nchunks2 > 0 && rowstaged_setup() == 0;
   const bool ring = ring_setup() == 0;
   const int unrolls[12] = {1, 2, 4, 0, 8, 9, 16, 17, 18, 19, 20, 21};
-  const int bps[5] = {2, 3, 4, 6, 8};
+  // grids beyond one resident wave let blocks that finish early take the
+  // remaining slices (the sweeps' slices are spread round-robin over warps)
+  const int bps[7] = {2, 3, 4, 6, 8, 12, 16};
   // UCPDHG_TUNE_LOG=1 prints every timed candidate to stderr
   const char* log_env = std::getenv("UCPDHG_TUNE_LOG");
   const bool log = log_env && log_env[0] == '1';
@@ -228,7 +230,7 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
       if ((U == 20 || U == 21) && !ring) continue;
       const int Us = (U == 2 || U == 4) ? U : 1;
       const int need = (nsl + kWarps * Us - 1) / (kWarps * Us);
-      for (int bi = 0; bi < 5; ++bi) {
+      for (int bi = 0; bi < 7; ++bi) {
         int g = std::min(w->num_sms * bps[bi], std::min(need, kMaxBlocks));
         if (g < 1) g = 1;
         k_reopen_state<<<1, 1, 0, s>>>(w->st);
