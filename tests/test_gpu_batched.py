@@ -71,3 +71,25 @@ def test_batched_nodes_bound_the_root():
     for r in rb:
         assert r["primal_obj"] >= root["primal_obj"] * (1 - 1e-7)
     ws.close()
+
+
+@pytest.mark.parametrize("rw,grid", [(1, 3), (2, 7), (4, 1)])
+def test_batched_fixed_shape(rw, grid):
+    """With the autotuner off, kernel_variant 1/2/4 and kernel_grid fix the
+    batched sweeps' rows (columns) per warp and blocks; tiny grids make each
+    warp sweep many row groups and the ragged tail.  Every node still reaches
+    rel-KKT 1e-8 as the oracle recomputes it."""
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    inst = build_instance(12, 18, 10, 12, seed=3, with_slack=True)
+    B = 8
+    l_b, u_b = node_fixings(inst, B)
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", tol=1e-8, time_limit_s=300.0, autotune=0,
+                                                    kernel_variant=rw, kernel_grid=grid))
+    xb, yb, rb = ws.solve_batched(l_b, u_b)
+    tb = ws.tuning()["batched"]
+    assert (tb["rows_per_warp_dual"], tb["grid_dual"], tb["rows_per_warp_adj"], tb["grid_adj"]) == (rw, grid, rw, grid)
+    xb, yb = xb.cpu().numpy(), yb.cpu().numpy()
+    for k in range(B):
+        assert rb[k]["status_name"] == "optimal", (k, rb[k])
+        assert kkt(_node_lp(inst, l_b[k], u_b[k]), xb[k], yb[k]).rel_kkt <= 1.5e-8
+    ws.close()
