@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(kBlock) k_kkt_col(IterArgs<T> a, int init) {
       const double v = __ldg(A.val + slot);
       const int c = __ldg(A.col + slot);
       e0 += v * (double)yc[c];
-      if (has_avg) e1 += v * ((double)yb[c] + (a.ybar64 ? a.ybar64[c] : 0.0));
+      // FP32 iterates: k_kkt_row has just flushed the window sums into ybar64
+      // and zeroed ybar, so the FP64 sum alone is the y-average sum
+      if (has_avg) e1 += v * (a.ybar64 ? a.ybar64[c] : (double)yb[c]);
     }
     const int j = s * kSlice + lane;
     if (j < a.n) {
