@@ -17,6 +17,10 @@ the autotuned launch configuration the bench uses.
 - Programmatic dependent launch of the per-attempt kernels (launch_overlap) gives
   bitwise the same iterates as plain launches over 256 adaptive attempts with
   the two variants the autotuner picks at this size, in both precisions.
+- Batched node LPs at the node-LP workload's full size (6049 buses, T = 48 with
+  shed/spill, 8 of the bench's node fixings in the 64-slot layout, 1280
+  adaptive attempts): the FP64 rel-KKT and objective the batched checks report
+  for every node equal the oracle's recomputation from the returned point.
 - The cp.async-ring variants (20, 21) sum every product in the order of the
   software-pipelined variant (0): on the same grid their iterates after 256
   adaptive attempts agree with it to FP32 (FP64) rounding of a contraction
@@ -128,3 +132,26 @@ def test_ring_variants_match_pipelined_full_size(full, precision, tol, variant):
     assert (rv["iterations"], rv["accepted"], rv["restarts"]) == (r0["iterations"], r0["accepted"], r0["restarts"])
     assert np.abs(xv - x0).max() <= tol * np.abs(x0).max()
     assert np.abs(yv - y0).max() <= tol * np.abs(y0).max()
+
+
+def test_batched_reported_rel_kkt_node_workload():
+    from oracle.lp import lp_from_arrays
+    from paper_2512_06715_gb300.instances import node_fixings, workload
+    from paper_2512_06715_gb300.pdhg import Workspace, default_opts
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    inst = workload("uc6049_g850_T48_slack")
+    B = 8
+    l_b, u_b = node_fixings(inst, B)
+    ws = Workspace.from_instance(inst, default_opts(precision="mixed", max_iters=1280, tol=1e-12,
+                                                    time_limit_s=300.0))
+    xb, yb, rb = ws.solve_batched(l_b, u_b)
+    xb, yb = xb.cpu().numpy(), yb.cpu().numpy()
+    ws.close()
+    for k in range(B):
+        assert rb[k]["iterations"] == 1280, rb[k]
+        lp = lp_from_arrays(inst.row_ptr, inst.col, inst.val, inst.q, inst.c, l_b[k], u_b[k], inst.m_eq)
+        chk = kkt(lp, xb[k], yb[k])
+        assert np.isfinite(chk.rel_kkt)
+        assert abs(chk.rel_kkt - rb[k]["rel_kkt"]) <= 1e-2 * rb[k]["rel_kkt"] + 1e-12, (k, chk.rel_kkt, rb[k])
+        assert abs(chk.primal_obj - rb[k]["primal_obj"]) <= 1e-8 * max(1.0, abs(chk.primal_obj)), k
