@@ -162,7 +162,6 @@ def dual_kernel_name(variant: int) -> str:
     second template argument of the sliced-ELL forms is the number of resident
     blocks per SM they are compiled for)."""
     return {0: "k_dual_pipe<float, 5>", 1: "k_dual<float, 1, 6>", 2: "k_dual<float, 2, 4>",
-            5: "k_dual<float, 2, 5>", 6: "k_dual_pipe<float, 6>",
             4: "k_dual<float, 4, 4>", 8: "k_dual<float, 1, 8>", 9: "k_dual_pipe<float, 8>",
             16: "k_dual_staged<float, 1>", 17: "k_dual_staged<float, 2>",
             18: "k_dual_rs<float, 1>", 19: "k_dual_rs<float, 2>",

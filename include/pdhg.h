@@ -115,7 +115,7 @@ typedef struct pdhg_opts {
                                fastest; 0: fixed defaults (1)                         */
   volatile int32_t *cancel_flag; /* host-mapped int polled at every check, or NULL    */
   int32_t kernel_variant;   /* -1: the autotuner decides, variant 1 when autotune is 0;
-                               0, 1, 2, 4, 5, 6, 8, 9, 16-21: that variant of both
+                               0, 1, 2, 4, 8, 9, 16-21: that variant of both
                                per-attempt kernels, as reported by pdhg_get_tuning,
                                with the default grid; read at the first solve of
                                each precision; batched solves with autotune 0: 1, 2

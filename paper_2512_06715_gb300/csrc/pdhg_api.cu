@@ -212,7 +212,7 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
   const bool staged = w->K.nchunks > 0 && w->KT.nchunks > 0 && staged_setup() == 0;
   const bool rowstaged = w->K.nchunks2 > 0 && w->KT.nchunks2 > 0 && rowstaged_setup() == 0;
   const bool ring = ring_setup() == 0;
-  const int unrolls[14] = {1, 2, 4, 0, 5, 6, 8, 9, 16, 17, 18, 19, 20, 21};
+  const int unrolls[12] = {1, 2, 4, 0, 8, 9, 16, 17, 18, 19, 20, 21};
   // grids beyond one resident wave let blocks that finish early take the
   // remaining slices (the sweeps' slices are spread round-robin over warps)
   const int bps[7] = {2, 3, 4, 6, 8, 12, 16};
@@ -223,12 +223,12 @@ static int autotune(Workspace* w, const IterArgs<T>& a, cudaStream_t s) {
     const int nsl = which == 0 ? w->K.nslices : w->KT.nslices;
     float best = 1e30f;
     int bu = 1, bg = which == 0 ? w->grid_k : w->grid_kt;
-    for (int ui = 0; ui < 14; ++ui) {
+    for (int ui = 0; ui < 12; ++ui) {
       const int U = unrolls[ui];
       if ((U == 16 || U == 17) && !staged) continue;
       if ((U == 18 || U == 19) && !rowstaged) continue;
       if ((U == 20 || U == 21) && !ring) continue;
-      const int Us = (U == 2 || U == 4 || U == 5) ? (U == 4 ? 4 : 2) : 1;
+      const int Us = (U == 2 || U == 4) ? U : 1;
       const int need = (nsl + kWarps * Us - 1) / (kWarps * Us);
       for (int bi = 0; bi < 7; ++bi) {
         int g = std::min(w->num_sms * bps[bi], std::min(need, kMaxBlocks));
@@ -353,12 +353,11 @@ static int validate_opts(const pdhg_opts* o) {
   if (o->fixed_eta < 0.0 || (o->fixed_eta > 0.0 && !(o->fixed_omega > 0.0)))
     return fail(PDHG_ERR_INVALID_ARG, "opts: fixed_eta needs fixed_omega > 0");
   if (!(o->kernel_variant == -1 || o->kernel_variant == 0 || o->kernel_variant == 1 ||
-        o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 5 ||
-        o->kernel_variant == 6 || o->kernel_variant == 8 ||
+        o->kernel_variant == 2 || o->kernel_variant == 4 || o->kernel_variant == 8 ||
         o->kernel_variant == 9 || o->kernel_variant == 16 || o->kernel_variant == 17 ||
         o->kernel_variant == 18 || o->kernel_variant == 19 || o->kernel_variant == 20 ||
         o->kernel_variant == 21))
-    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 5, 6, 8, 9 or 16-21");
+    return fail(PDHG_ERR_INVALID_ARG, "opts: kernel_variant must be -1, 0, 1, 2, 4, 8, 9 or 16-21");
   if (o->ir_fold_checks < 0)
     return fail(PDHG_ERR_INVALID_ARG, "opts: ir_fold_checks must be >= 0");
   if (o->launch_overlap != 0 && o->launch_overlap != 1)

@@ -644,8 +644,7 @@ void launch_init_iterates(const IterArgs<T>& a, int grid, cudaStream_t s) {
   }
 }
 
-// Variants: 1, 2, 4 slices per warp; 0 software pipelined; 5 and 6 the
-// two-slice and pipelined forms at one more resident block per SM; 8 and 9 the
+// Variants: 1, 2, 4 slices per warp; 0 software pipelined; 8 and 9 are the
 // one-slice and the pipelined forms compiled for 8 resident blocks per SM
 // (at most 32 registers, a few spilled to L1) -- more warps in flight against
 // the HBM and L2 latency at the cost of the spills; 16 and 17 stage the matrix
@@ -664,14 +663,6 @@ struct MinBlocks {
 template <class T>
 struct MinBlocksPipe {
   static constexpr int value = sizeof(T) == 4 ? 5 : 3;
-};
-// Variants 5 and 6: the two-slice and the pipelined forms one resident block
-// per SM further (two slices: 48 FP32 / 64 FP64 registers without spills;
-// pipelined: 40 / 64 registers with a few spills to L1).
-template <class T>
-struct MinBlocksDense {
-  static constexpr int two = sizeof(T) == 4 ? 5 : 4;
-  static constexpr int pipe = sizeof(T) == 4 ? 6 : 4;
 };
 
 // One per-attempt kernel, with the programmatic-dependent-launch attribute when
@@ -702,8 +693,6 @@ void launch_dual(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) {
     case 0: launch_iter<T>(k_dual_pipe<T, MinBlocksPipe<T>::value>, a, grid, s); break;
     case 2: launch_iter<T>(k_dual<T, 2, MinBlocks<T, 2>::value>, a, grid, s); break;
     case 4: launch_iter<T>(k_dual<T, 4, MinBlocks<T, 4>::value>, a, grid, s); break;
-    case 5: launch_iter<T>(k_dual<T, 2, MinBlocksDense<T>::two>, a, grid, s); break;
-    case 6: launch_iter<T>(k_dual_pipe<T, MinBlocksDense<T>::pipe>, a, grid, s); break;
     case 8: launch_iter<T>(k_dual<T, 1, 8>, a, grid, s); break;
     case 9: launch_iter<T>(k_dual_pipe<T, 8>, a, grid, s); break;
     case 16: launch_dual_staged<T>(a, grid, s, 1); break;
@@ -722,8 +711,6 @@ void launch_adjoint(const IterArgs<T>& a, int grid, cudaStream_t s, int unroll) 
     case 0: launch_iter<T>(k_adjoint_pipe<T, MinBlocksPipe<T>::value>, a, grid, s); break;
     case 2: launch_iter<T>(k_adjoint<T, 2, MinBlocks<T, 2>::value>, a, grid, s); break;
     case 4: launch_iter<T>(k_adjoint<T, 4, MinBlocks<T, 4>::value>, a, grid, s); break;
-    case 5: launch_iter<T>(k_adjoint<T, 2, MinBlocksDense<T>::two>, a, grid, s); break;
-    case 6: launch_iter<T>(k_adjoint_pipe<T, MinBlocksDense<T>::pipe>, a, grid, s); break;
     case 8: launch_iter<T>(k_adjoint<T, 1, 8>, a, grid, s); break;
     case 9: launch_iter<T>(k_adjoint_pipe<T, 8>, a, grid, s); break;
     case 16: launch_adjoint_staged<T>(a, grid, s, 1); break;

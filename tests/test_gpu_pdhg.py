@@ -89,7 +89,7 @@ def test_spmv_and_scaling_parity(shape):
 
 @pytest.mark.parametrize("variant,grid", [(-1, 0), (1, 3), (2, 3), (4, 2), (0, 0), (0, 3), (8, 3), (9, 2),
                                           (16, 0), (16, 3), (17, 2), (18, 0), (18, 3), (19, 2),
-                                          (20, 0), (20, 3), (21, 2), (5, 0), (5, 3), (6, 0), (6, 2)])
+                                          (20, 0), (20, 3), (21, 2)])
 def test_fixed_step_iterates_match_oracle(tiny24, variant, grid):
     """Constant steps, no restarts: iterates after 128 attempts agree with the
     oracle to 1e-10 relative, for every variant of the per-attempt kernels
@@ -134,7 +134,7 @@ def test_solve_tiny_matches_oracle(tiny24, tiny24_oracle, precision):
     assert r["time_to_tol"][0] > 0 and r["time_to_tol"][2] >= r["time_to_tol"][0]
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4, 5, 6, 8, 9, 16, 17, 18, 19, 20, 21])
+@pytest.mark.parametrize("variant", [0, 2, 4, 8, 9, 16, 17, 18, 19, 20, 21])
 def test_fp32_kernel_variants_solve(tiny24, tiny24_oracle, variant):
     """Each non-default FP32 variant on a 3-block grid (every warp sweeps many
     slices and the ragged last one) solves the 24-bus relaxation to rel-KKT 1e-8
@@ -153,7 +153,7 @@ def test_fp32_kernel_variants_solve(tiny24, tiny24_oracle, variant):
     ws.close()
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4, 5, 6, 8, 9, 16, 17, 18, 19, 20, 21])
+@pytest.mark.parametrize("variant", [0, 2, 4, 8, 9, 16, 17, 18, 19, 20, 21])
 def test_fp32_kernel_variants_fixed_step(tiny24, variant):
     """FP32 iterates of every kernel variant on 3 blocks (each warp sweeps many
     slices and the ragged last one) equal those of the one-slice variant on the
