@@ -325,8 +325,9 @@ int pdhg_get_trace(void *ws, double *attempts, int64_t cap_a, double *checks, in
  * loaded while the current slice's gathers are in flight); 8, 9: variants 1
  * and 0 compiled for 8 resident blocks per SM (32 registers); 16, 17: the matrix
  * staged in shared memory by TMA bulk copies, one or two slices per warp at a
- * time; 18, 19: the same with the row (column) operands staged too.  A
- * precision not yet solved reports unroll -1 and grid 0. */
+ * time; 18, 19: the same with the row (column) operands staged too; 20, 21:
+ * a per-warp shared-memory ring filled by cp.async two or three slices ahead.
+ * A precision not yet solved reports unroll -1 and grid 0. */
 int pdhg_get_tuning(void *ws, int32_t *cfg);
 
 /* Launch the two per-attempt kernels of `precision` `reps` times each on
