@@ -135,3 +135,28 @@ def test_node_results_gather_gloo():
     for rank in (0, 1):
         assert [d["node"] for d in got[rank]] == list(range(9))
         assert [d["rank"] for d in got[rank]] == [0] * 5 + [1] * 4
+
+
+def test_every_autotuner_variant_names_its_kernel_and_source():
+    """The roofline line names the K x' kernel of whatever variant the autotuner
+    picks and looks its DRAM record up under that kernel's source file: every
+    variant the autotuner times maps to a template instance defined in the file
+    named, and the committed record's kernels are among them."""
+    import re
+    sys.path.insert(0, str(ROOT))
+    import bench
+    api = (ROOT / "paper_2512_06715_gb300" / "csrc" / "pdhg_api.cu").read_text()
+    m = re.search(r"const int unrolls\[\d+\] = \{([^}]*)\}", api)
+    variants = [int(v) for v in m.group(1).split(",")]
+    names = set()
+    for v in variants:
+        name = bench.dual_kernel_name(v)
+        assert not name.startswith("variant"), v
+        base = name.split("<")[0]
+        src = bench.dual_kernel_source(v)
+        assert src.exists() and re.search(r"\b%s\s*\(" % base, src.read_text()), (v, name, src)
+        names.add(name)
+    recs = json.loads((ROOT / "profiles" / "dram_traffic.json").read_text())
+    for r in recs:
+        assert r["kernel"] in names, r["kernel"]
+        assert (ROOT / r["source"]).exists(), r["source"]
