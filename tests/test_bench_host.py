@@ -160,3 +160,29 @@ def test_every_autotuner_variant_names_its_kernel_and_source():
     for r in recs:
         assert r["kernel"] in names, r["kernel"]
         assert (ROOT / r["source"]).exists(), r["source"]
+
+
+def test_write_trace_table(tmp_path):
+    """The per-check trace summary: the array is saved, the table lists about 40
+    evenly spaced checks plus every restart, with the command that made it."""
+    import numpy as np
+    sys.path.insert(0, str(ROOT))
+    import bench
+    n = 200
+    checks = np.zeros((n, 12))
+    checks[:, 0] = 64 * np.arange(1, n + 1)
+    checks[[3, 77, 150], 1] = 1           # restarts
+    checks[77, 2] = 1                     # one of them to the average
+    checks[:, 3] = 2.0
+    checks[:, 6] = np.logspace(0, -6, n)  # rel-KKT of the current iterate
+    checks[:, 7] = np.logspace(0, -7, n)
+    r = {"status_name": "time_limit", "rel_kkt": 1e-7, "iterations": 64 * n, "restarts": 3, "ir_rounds": 5,
+         "omega": 2.0, "time_to_tol": [1.0, 2.0, -1.0]}
+    bench.write_trace(tmp_path, "case_mixed", checks, r, {"bound_obj_rescale": 1})
+    assert np.array_equal(np.load(tmp_path / "trace_case_mixed.npy"), checks)
+    md = (tmp_path / "trace_case_mixed.md").read_text()
+    rows = [l for l in md.splitlines() if l.startswith("| ") and l[2].isdigit()]
+    assert 40 <= len(rows) <= 43
+    assert any(l.startswith("| 4992 | yes (avg)") for l in rows)  # check 77 (0-based, 64 x 78 attempts): to the average
+    assert any(l.startswith("| 256 | yes |") for l in rows)
+    assert "python " in md and "bound_obj_rescale" in md
