@@ -43,6 +43,7 @@ def test_opts_default(lib):
     assert o.beta_sufficient == 0.2 and o.beta_necessary == 0.8 and o.beta_artificial == 0.36
     assert o.precision == pdhg.PREC_FP64
     assert o.kernel_variant == -1 and o.kernel_grid == 0 and o.autotune == 1
+    assert o.infeas_tol == 1e-8 and o.ir_fold_checks == 16 and o.launch_overlap == 0
 
 
 def test_invalid_arguments_rejected_on_host(lib):
@@ -63,7 +64,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     o = pdhg.default_opts()
     o.precision = 7
     assert lib.pdhg_workspace_create(C.byref(prob), C.byref(o), C.byref(ws), None) == -1
-    for field, bad in (("kernel_variant", 3), ("kernel_variant", -2), ("kernel_grid", -1)):
+    for field, bad in (("kernel_variant", 3), ("kernel_variant", -2), ("kernel_variant", 22), ("kernel_grid", -1),
+                       ("kernel_grid", 8193), ("launch_overlap", 2), ("ir_fold_checks", -1)):
         o = pdhg.default_opts()
         setattr(o, field, bad)
         assert lib.pdhg_workspace_create(C.byref(prob), C.byref(o), C.byref(ws), None) == -1
